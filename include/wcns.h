@@ -1,0 +1,204 @@
+/*
+ * wcns.h -- C ABI of the WCNS-FE solver library (libwcns.so) for one GB300 GPU.
+ *
+ * The library evaluates the right-hand side of the semi-discrete conservation law
+ * du_i/dt = -df/dx|_i (Sec. 2, Eq. 1-2) with the filtered embedded weighted compact
+ * nonlinear scheme of Liu, Min, Cai, Ma and Yan (arXiv 2306.09760) and advances it
+ * with third-order TVD Runge-Kutta.  Per sweep direction and interface i+1/2:
+ *   (a) project the six stencil states U_{i-2..i+3} onto characteristic fields with
+ *       Roe-averaged eigenvectors (Euler), or use them as they are (advection);
+ *   (b) interpolate each field to the midpoint from the sub-stencils S0, S1, S2
+ *       (Eq. 5), with smoothness indicators (Eq. 9-10), JS / Z / M weights
+ *       (Eq. 11-15) and the FE mapping function (Eq. 20-21, Table 2) or its PFE
+ *       switch (App. A), for the left state and the mirrored right state;
+ *   (c) form the midpoint flux with an approximate Riemann solver (Eq. 6);
+ *   (d) take the sixth-order midpoint flux difference (Eq. 3);
+ *   (e) apply a TVD-RK3 stage.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays ("state buffers") live in device memory unless a function says "host".
+ *     The caller owns them; the library never frees or retains them past the call's
+ *     stream work.  Layout: element (v, j, i) of a grid buffer is at offset
+ *     (v * ny + j) * pitch + i elements -- structure of arrays, one plane per
+ *     conserved variable v, rows j of `pitch` elements, cells i contiguous.
+ *     Element type: double (WCNS_F64) or float (WCNS_F32), fixed per context.
+ *     Device pointers must be 16-byte aligned.
+ *   - Conserved variables: advection (u); Euler 1D (rho, rho u, E); Euler 2D
+ *     (rho, rho u, rho v, E), ideal gas p = (gamma - 1)(E - rho |v|^2 / 2).
+ *   - Ghost cells are not stored: boundary conditions are applied by index
+ *     arithmetic (periodic: modulo; transmissive: the nearest interior cell).
+ *   - All work is enqueued asynchronously on the context's CUDA stream (the stream
+ *     handle passed at creation; NULL = the legacy default stream).  Functions that
+ *     return results to the host synchronise that stream and say so.
+ *   - Errors: argument errors are returned at once and nothing is enqueued.  Errors
+ *     the device detects (non-physical state, an expired bounded wait) are sticky:
+ *     they are recorded in device memory and returned by wcns_sync_status().  No
+ *     C++ exception crosses this interface and no kernel traps.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef WCNS_H_
+#define WCNS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WCNS_OK = 0,
+  WCNS_ERR_ARG = 1,          /* invalid argument (null, size, alignment, enum value) */
+  WCNS_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  WCNS_ERR_NONPHYSICAL = 3,  /* a cell state had rho <= 0, p <= 0 or NaN (sticky) */
+  WCNS_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired (sticky) */
+  WCNS_ERR_UNSUPPORTED = 5,  /* option combination not implemented */
+  WCNS_ERR_NOMEM = 6         /* device allocation failed */
+} wcns_status;
+
+enum { WCNS_F64 = 0, WCNS_F32 = 1 };                            /* element type */
+enum { WCNS_BC_PERIODIC = 0, WCNS_BC_TRANSMISSIVE = 1 };        /* boundary per direction */
+enum { WCNS_ADVECTION = 0, WCNS_EULER = 1 };                    /* equation system */
+/* Weights: JS (Eq. 11), Z (Eq. 14-15), FE = Z weights mapped by Eq. 20 and
+ * renormalised, PFE = FE with the App. A switch, M = Henrick mapping (Eq. 12-13). */
+enum { WCNS_W_JS = 0, WCNS_W_Z = 1, WCNS_W_FE = 2, WCNS_W_PFE = 3, WCNS_W_M = 4 };
+/* Midpoint flux (Eq. 6; the paper names no solver): local Lax-Friedrichs, Roe with
+ * Harten's entropy fix on the acoustic fields, HLLC with Einfeldt speeds, and
+ * Lax-Friedrichs with a frozen dissipation speed alpha[d] (smooth; for adjoints). */
+enum { WCNS_FLUX_LLF = 0, WCNS_FLUX_ROE = 1, WCNS_FLUX_HLLC = 2, WCNS_FLUX_LLF_FROZEN = 3 };
+enum { WCNS_REDUCE_SUM = 0, WCNS_REDUCE_L1 = 1, WCNS_REDUCE_LINF = 2, WCNS_REDUCE_MAXWAVE = 3 };
+
+/* Grid descriptor (Sec. 2: uniform cells, h = (hi - lo) / n per direction). */
+typedef struct {
+  int32_t ndim;      /* 1 or 2 */
+  int32_t nvar;      /* 1 (advection), 3 (Euler, ndim 1), 4 (Euler, ndim 2) */
+  int32_t dtype;     /* WCNS_F64 or WCNS_F32 */
+  int32_t reserved;  /* must be 0 */
+  int64_t nx, ny;    /* cells; ny = 1 when ndim = 1; 1 <= nx, ny <= 2^26 */
+  int64_t pitch;     /* elements per row; pitch >= nx and pitch % 32 == 0 */
+  double lo[2], hi[2];
+  int32_t bc[2];     /* WCNS_BC_* for x and y */
+} wcns_grid;
+
+/* Scheme parameters.  wcns_default_params() fills the defaults named below. */
+typedef struct {
+  int32_t system;          /* WCNS_ADVECTION or WCNS_EULER */
+  int32_t weights;         /* WCNS_W_*; default FE */
+  int32_t flux;            /* WCNS_FLUX_*; default HLLC */
+  int32_t characteristic;  /* 1: interpolate characteristic variables (default); 0: conserved */
+  int32_t z_p;             /* Z-weight exponent p of Eq. 14, 1 or 2; default 1 */
+  int32_t renorm;          /* 1: renormalise the mapped weights (default) */
+  int32_t reserved[2];     /* must be 0 */
+  double adv_speed[2];     /* advection speed per direction (advection only) */
+  double gamma;            /* ratio of specific heats; default 1.4 */
+  double eps;              /* epsilon of Eq. 11 / Eq. 14; default 1e-40 (F64), 1e-30 (F32) */
+  double xi, kappa;        /* steepness and null-point parameters of Eq. 20; default 1e6, 0.5 */
+  double cv;               /* PFE switch width (App. A); default 1e-3 */
+  double cfl;              /* CFL number for automatic steps; default 0.5 */
+  double alpha[2];         /* frozen Lax-Friedrichs speeds (WCNS_FLUX_LLF_FROZEN) */
+  double harten;           /* Roe entropy-fix width delta = harten * (|u| + c); default 0.1 */
+} wcns_params;
+
+typedef struct wcns_ctx wcns_ctx;
+typedef struct wcns_batch wcns_batch;
+
+/* Fills *p with the defaults for `system` and element type `dtype`.  Returns
+ * WCNS_ERR_ARG on a null pointer or unknown enum. */
+wcns_status wcns_default_params(int32_t system, int32_t dtype, wcns_params* p);
+
+/* Creates a context for one grid.  Validates *grid and *params, copies them, and
+ * allocates the context's own device scratch: two stage states (2 x nvar*ny*pitch
+ * elements), one x-sweep RHS plane set (2D), the device time and step size, and
+ * reduction partials.  `stream` is a cudaStream_t (NULL: default stream).
+ * Errors: WCNS_ERR_ARG (invalid descriptor), WCNS_ERR_UNSUPPORTED (nvar does not
+ * match system/ndim), WCNS_ERR_NOMEM, WCNS_ERR_CUDA.  On error *out is NULL. */
+wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* stream,
+                      wcns_ctx** out);
+
+/* dudt = L(u) = -(dF/dx + dG/dy), Eq. 2-3, steps (a)-(d) of the header comment.
+ * u and dudt: device grid buffers; they must not overlap. */
+wcns_status wcns_rhs(wcns_ctx* ctx, const void* u, void* dudt);
+
+/* Advances u in place by nsteps TVD-RK3 steps (Shu-Osher form):
+ *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),  u <- 1/3 u + 2/3 (u2 + dt L(u2)).
+ * dt > 0: fixed step.  dt <= 0: each step takes dt = cfl / sum_d(max(|u_d| + c) / h_d)
+ * (advection: |a_d| for max(|u_d| + c)), reduced on the device, never read back.
+ * t_end > 0: each step is clipped so the device time t never passes t_end; once t
+ * reaches t_end further steps do nothing.  The device time starts at 0 (see
+ * wcns_set_time) and is read with wcns_get_time.  Asynchronous. */
+wcns_status wcns_step(wcns_ctx* ctx, void* u, double dt, int32_t nsteps, double t_end);
+
+/* wcns_step on a HOST buffer u_host (same layout; pinned memory is fastest): copies
+ * it to the context's device state, steps, and copies the result back, all on the
+ * context stream; returns after the copy back completes. */
+wcns_status wcns_step_host(wcns_ctx* ctx, void* u_host, double dt, int32_t nsteps, double t_end);
+
+/* Device time control.  wcns_get_time synchronises the stream and returns the
+ * device time and the number of steps that advanced it since the last set. */
+wcns_status wcns_set_time(wcns_ctx* ctx, double t);
+wcns_status wcns_get_time(wcns_ctx* ctx, double* t, int64_t* steps_taken);
+
+/* Reductions over a grid buffer, results in FP64 on the host (synchronises).
+ *   WCNS_REDUCE_SUM:     out[v] = sum over cells of a[v]            (nvar values)
+ *   WCNS_REDUCE_L1:      out[v] = mean over cells of |a[v] - b[v]|  (b NULL: |a|)
+ *   WCNS_REDUCE_LINF:    out[v] = max over cells of |a[v] - b[v]|   (b NULL: |a|)
+ *   WCNS_REDUCE_MAXWAVE: out[d] = max over cells of |u_d| + c       (ndim values)
+ * Accumulation is FP64 for both element types. */
+wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t what, double* out);
+
+/* Adjoint of one TVD-RK3 step of fixed size dt: given u_n and the cotangent lam_np1
+ * of u_{n+1} = S(u_n), writes lam_n = (dS/du_n)^T lam_np1.  The stage states are
+ * recomputed from u_n.  Supported: WCNS_EULER, ndim 2, WCNS_FLUX_LLF_FROZEN, weights
+ * JS / Z / FE, characteristic 0 or 1; otherwise WCNS_ERR_UNSUPPORTED.  lam_np1 and
+ * lam_n may be the same buffer.  Asynchronous. */
+wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const void* lam_np1,
+                              void* lam_n);
+
+/* Synchronises the context stream and returns (then clears) the sticky device
+ * error; *nonphysical_interfaces (may be NULL) receives the number of interfaces
+ * whose interpolated states fell back to the cell states since the last call. */
+wcns_status wcns_sync_status(wcns_ctx* ctx, int64_t* nonphysical_interfaces);
+
+const char* wcns_status_string(wcns_status s);
+
+/* Releases the context and its scratch (synchronises its stream first). */
+void wcns_destroy(wcns_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batched 1D Euler problems (many independent uneven grids, one launch per stage).
+ * Problem k occupies columns offsets[k] .. offsets[k] + n[k] - 1 of a concatenated
+ * buffer with `nvar` = 3 planes of `total` elements each (plane stride `total`),
+ * on the domain [lo, hi] with boundary `bc` on both ends.  Every problem takes its
+ * own CFL step each RK3 step; work is scheduled over (problem, tile) items by
+ * persistent kernels, and each RK3 step replays one captured CUDA graph.
+ * ------------------------------------------------------------------------- */
+
+/* Creates a batch context.  offsets/n are host arrays of nprob entries; problems must
+ * not overlap and must lie inside [0, total).  Copies them; allocates the stage
+ * states, per-problem dt and time, and the work list (sorted by size, largest first).
+ * `tile` = 0 lets the autotuner pick the tile (cells per work item) and the number of
+ * resident blocks per SM on the first wcns_batch_step; otherwise one of 123, 251, 507. */
+wcns_status wcns_batch_init(const int64_t* offsets, const int64_t* n, int32_t nprob, int64_t total,
+                            double lo, double hi, int32_t bc, const wcns_params* params,
+                            int32_t dtype, int32_t tile, void* stream, wcns_batch** out);
+
+/* nsteps TVD-RK3 steps of every problem, each with its own CFL step clipped at t_end
+ * (t_end <= 0: unclipped).  u_concat: device buffer described at wcns_batch_init.
+ * Asynchronous (graph replays on the batch stream). */
+wcns_status wcns_batch_step(wcns_batch* b, void* u_concat, int32_t nsteps, double t_end);
+
+/* Reports the autotuned (or fixed) tile and blocks per SM, and the number of
+ * candidates the autotuner timed (0 if fixed). */
+wcns_status wcns_batch_config(wcns_batch* b, int32_t* tile, int32_t* blocks_per_sm,
+                              int32_t* candidates_timed);
+
+/* Per-problem device times (host array of nprob doubles); synchronises. */
+wcns_status wcns_batch_times(wcns_batch* b, double* t_host);
+
+wcns_status wcns_batch_sync_status(wcns_batch* b, int64_t* nonphysical_interfaces);
+void wcns_batch_destroy(wcns_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCNS_H_ */
