@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the WCNS-FE hot path (one TVD-RK3 step = one "step").
+
+Workload: 2D Euler, 2048 x 2048 cells, four-quadrant Riemann data with seeded states
+(split at x = y = 0.8), transmissive boundaries, CFL 0.5, FE weights (xi = 1e6,
+kappa = 0.5), HLLC flux, characteristic projection; FP32 bulk arithmetic.  A step is
+the CFL reduction plus three stages of (x sweep, y sweep + stage update).
+
+Prints one JSON line.  `value` is the whole-job cell-update rate (Mcell-updates/s,
+cell-updates of all ranks / max-over-ranks time).  Several GPUs run independent
+replicas (the path has no exchange step on one grid per GPU): weak scaling.
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-updates/s per RK3 step (FP64 vs FP32, adjoint) and % of HBM roofline"
+UNIT = "Mcell-updates/s"
+N_MAIN = 2048
+SEED = 0
+# FP32 bulk: 8 array passes of 4 variables x 4 bytes per cell-update (stage 1 reads
+# u^n and writes u1; stages 2-3 read u^n and u^(k-1) and write) = 128 B.
+ALG_BYTES_PER_CELL_UPDATE = {"f32": 128, "f64": 256}
+# Peaks: HBM from the measured copy bandwidth; ALU peaks derived from unit counts and
+# the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; FP64 nominal).
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_ALU_PEAK_TFLOPS = 1.25
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2306_09760_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode() + open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_kind: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, or
+    None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[kernel_kind]
+        if e.get("source_digest") != kernel_source_digest():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def flops_per_cell_rhs(problem_small, dtype):
+    """Algorithmic flops of one RHS evaluation per cell (exact operation count of the
+    oracle's plain restatement of the method on the same kind of data)."""
+    import oracle
+    return oracle.count_rhs_flops(problem_small) / (problem_small.nx * problem_small.ny)
+
+
+def cpu_sample_rate(seconds_target=15.0, steps_hint=None):
+    """Times the oracle on a band of the same 2048-wide workload (128 rows around the
+    y = 0.8 quadrant line, transmissive band edges)."""
+    import numpy as np
+    import oracle
+    from paper_2306_09760_gb300 import inputs
+    P = inputs.riemann2d(N_MAIN, seed=SEED)
+    j0 = int(0.8 * N_MAIN) - 64
+    band = P.u0[:, j0:j0 + 128, :].copy()
+    Q = inputs.Problem("band", 2, 4, N_MAIN, 128, (0.0, 0.0), (1.0, 128.0 / N_MAIN), (1, 1), band, 1)
+    u = band
+    t0 = time.perf_counter()
+    u, _, _, _ = oracle.step(Q, u, nsteps=1)
+    one = time.perf_counter() - t0
+    steps = steps_hint or max(1, int(seconds_target / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    u, _, _, _ = oracle.step(Q, u, nsteps=steps)
+    wall = time.perf_counter() - t0
+    cells = Q.nx * Q.ny
+    return {"value": cells * steps / wall / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{steps} TVD-RK3 step(s) of a 2048 x 128 band (rows {j0}..{j0 + 127}) of the 2048^2 "
+                      f"workload, FP64 oracle, {wall:.1f} s"}, wall, steps
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import numpy as np
+    from paper_2306_09760_gb300 import inputs
+    P = inputs.riemann2d(N_MAIN, seed=SEED)
+    j0 = int(0.8 * N_MAIN) - 64
+    band = P.u0[:, j0:j0 + 128, :].copy()
+    Q = inputs.Problem("band", 2, 4, N_MAIN, 128, (0.0, 0.0), (1.0, 128.0 / N_MAIN), (1, 1), band, 1)
+    u = band
+    for _ in range(args.warmup):
+        u, _, _, _ = oracle.step(Q, u, nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _, _, _ = oracle.step(Q, u, nsteps=1)
+    wall = time.perf_counter() - t0
+    cells = Q.nx * Q.ny
+    value = cells * args.steps / wall / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D Euler 2048x2048 four-quadrant Riemann (seed 0), FP64 CPU oracle on a "
+                               "2048x128 band per step", "global_batch": 1, "seq_len": N_MAIN,
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"2048x128 band of the 2048^2 workload per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_solver(W, torch, S, stream, steps, warmup, profile=True):
+    S.step(0.0, warmup)
+    torch.cuda.synchronize()
+    if profile:
+        W.wcns_profile_enable(S.ctx, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.step(0.0, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = W.wcns_profile_read(S.ctx) if profile else {}
+    if profile:
+        W.wcns_profile_enable(S.ctx, False)
+    return ms, prof
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2306_09760_gb300 import build as wbuild
+    if rank == 0:
+        wbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2306_09760_gb300 import inputs, wcns as W
+    W.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    P = inputs.riemann2d(N_MAIN, seed=SEED)
+    ncell = P.nx * P.ny
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f32", stream=stream)
+        S.step(0.0, args.warmup)
+        torch.cuda.synchronize()
+        W.wcns_profile_enable(S.ctx, True)
+        W.wcns_profile_read(S.ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            S.step(0.0, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        ms = e0.elapsed_time(e1)
+        prof = W.wcns_profile_read(S.ctx)
+        W.wcns_profile_enable(S.ctx, False)
+        st, nonph = S.status()
+        if st != W.WCNS_OK:
+            raise RuntimeError(f"device status after the timed region: {W.wcns_status_string(st)}")
+        t_sim, steps_taken = S.time()
+
+        # e2e: the public host-buffer entry point, copies inside the timed region
+        host = torch.zeros((S.grid.nvar, S.grid.ny, S.grid.pitch), dtype=torch.float32).pin_memory()
+        host[:, :, :P.nx] = torch.from_numpy(P.u0).float()
+        e2e_steps = max(1, min(args.steps, 10))
+        W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
+        e2e_wall = time.perf_counter() - t0
+        barrier()
+        S.close()
+
+    ms_t = torch.tensor([ms, e2e_wall], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(ms_t[0]), float(ms_t[1])
+    value = world * ncell * args.steps / (ms_max / 1e3) / 1e6
+    e2e_value = world * ncell * e2e_steps / e2e_max / 1e6
+    state_bytes = S.grid.nvar * S.grid.ny * S.grid.pitch * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # dominant kernel and its roofline (algorithmic flops per launch / event duration)
+    import oracle
+    oracle.build()
+    dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
+    launches, tot_ms = prof[dom]
+    flops_cell = flops_per_cell_rhs(inputs.riemann2d(64, seed=SEED), "f32")
+    per_dir = flops_cell / 2.0
+    stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0}.get(dom, 0)
+    flops_per_launch = ncell * (per_dir + stage_extra)
+    achieved_tflops = flops_per_launch / (tot_ms / launches / 1e3) / 1e12
+    hbm_peak, hbm_kind = measured_peaks()
+    alg_gbs = value * 1e6 * ALG_BYTES_PER_CELL_UPDATE["f32"] / 1e9
+    traffic = ncu_traffic(dom)
+    gpu_launches = sum(v[0] for v in prof.values())
+
+    variants = {}
+    if not args.no_variants:
+        variants = run_variants(args, W, torch, inputs, hbm_peak)
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu, _, _ = cpu_sample_rate(seconds_target=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2D Euler 2048x2048, four-quadrant Riemann data (seed 0, split x=y=0.8), "
+                               "transmissive, CFL 0.5, WCNS-FE (xi=1e6, kappa=0.5), HLLC, characteristic; FP32 bulk",
+                   "global_batch": world, "seq_len": N_MAIN, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2: each stage touches 4 state-size arrays (256 MiB) > 126 MiB L2",
+                   "simulated_time": t_sim, "steps_taken": steps_taken, "fallback_interfaces": nonph},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "flops_per_launch": flops_per_launch, "launch_ms": tot_ms / launches},
+        "hbm": {"achieved_gbs": alg_gbs, "peak_gbs": hbm_peak, "frac": alg_gbs / hbm_peak,
+                "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE["f32"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},
+        "clocks": clk.summary(),
+        "gpu_launches": gpu_launches,
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]},
+        "variants": variants,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_variants(args, W, torch, inputs, hbm_peak):
+    """Secondary workloads of the same metric (short runs)."""
+    out = {}
+    stream = torch.cuda.Stream()
+    cases = [
+        ("euler2d_2048_f64", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f64", 2, 1, {}),
+        ("sod_4096_f64", lambda: inputs.sod(4096), "f64", 200, 20, {}),
+        ("sod_4096_f32", lambda: inputs.sod(4096), "f32", 200, 20, {}),
+        ("shu_osher_4096_f64", lambda: inputs.shu_osher(4096), "f64", 200, 20, {}),
+        ("euler2d_2048_f32_xi100", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f32", 10, 3, dict(xi=100.0)),
+        ("advection_200_f64", lambda: inputs.advection_sine(200), "f64", 400, 20, {}),
+    ]
+    for name, make, dt, steps, warm, params in cases:
+        P = make()
+        with torch.cuda.stream(stream):
+            S = W.Solver(P, dt, stream=stream, **params)
+            ms, prof = time_solver(W, torch, S, stream, steps, warm, profile=False)
+            S.close()
+        rate = P.nx * P.ny * steps / (ms / 1e3) / 1e6
+        nbytes = ALG_BYTES_PER_CELL_UPDATE[dt] * P.nvar / 4 if P.nvar != 4 else ALG_BYTES_PER_CELL_UPDATE[dt]
+        out[name] = {"value": rate, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                     "hbm_frac": rate * 1e6 * nbytes / 1e9 / hbm_peak}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

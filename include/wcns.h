@@ -160,6 +160,18 @@ wcns_status wcns_sync_status(wcns_ctx* ctx, int64_t* nonphysical_interfaces);
 
 const char* wcns_status_string(wcns_status s);
 
+/* Per-kernel timing for benchmarks (no counterpart in the paper).  While enabled,
+ * every kernel the context launches is bracketed by CUDA events recorded on the
+ * context stream, and wcns_step launches kernels directly instead of replaying its
+ * captured graph.  Enabling (or disabling) discards unread records. */
+wcns_status wcns_profile_enable(wcns_ctx* ctx, int32_t on);
+
+/* Synchronises the stream and returns, per kernel kind, its name (48-byte slots in
+ * `names`), launches and total milliseconds since the last read, then resets them.
+ * max_entries must be >= 7 (the number of kinds); *n_entries receives that number. */
+wcns_status wcns_profile_read(wcns_ctx* ctx, int32_t max_entries, char* names, int64_t* launches,
+                              double* ms, int32_t* n_entries);
+
 /* Releases the context and its scratch (synchronises its stream first). */
 void wcns_destroy(wcns_ctx* ctx);
 

@@ -83,6 +83,8 @@ def lib():
         L.oracle_eigenvectors.restype = None
         L.oracle_eigenvectors.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, dp, dp]
+        L.oracle_interface_flux.restype = ctypes.c_int
+        L.oracle_interface_flux.argtypes = [cp, dp, dp]
         L.oracle_riemann.restype = None
         L.oracle_riemann.argtypes = [cp, dp, dp, dp]
         L.oracle_rhs.restype = ctypes.c_longlong
@@ -191,6 +193,17 @@ def riemann(UL, UR, nvar, **params):
     F = np.zeros(nvar)
     lib().oracle_riemann(ctypes.byref(c), _dp(a), _dp(b), _dp(F))
     return F
+
+
+def interface_flux(S, nvar, system=1, ax=1.0, **params):
+    """Midpoint flux between cells 2 and 3 of six stencil states S[6, nvar] (x normal).
+    Returns (F, fell_back)."""
+    c = make_cfg(None, **params)
+    c.nvar, c.system, c.ax = nvar, system, ax
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    F = np.zeros(nvar)
+    fb = lib().oracle_interface_flux(ctypes.byref(c), _dp(S), _dp(F))
+    return F, bool(fb)
 
 
 def rhs(problem, u=None, **params):

@@ -733,6 +733,16 @@ void oracle_eigenvectors(int nvar, double gamma, double u, double v, double H, d
     }
 }
 
+// Midpoint flux at the interface between cells 2 and 3 of six stencil states
+// S[m][v] (m = 0..5 = cells i-2..i+3, x-normal ordering); returns 1 on fallback.
+int oracle_interface_flux(const oracle_cfg* c, const double* S, double* F) {
+  const int nv = c->nvar;
+  auto cell = [&](int64_t m, int v) -> double { return S[m * nv + v]; };
+  Stats st{0, nullptr, 0, 0};
+  interface_flux<double>(2, 6, 1, *c, (c->system == 0) ? c->ax : c->alpha_x, cell, F, &st);
+  return (int)st.nonphysical;
+}
+
 // Midpoint Riemann flux of two states in the x normal.
 void oracle_riemann(const oracle_cfg* c, const double* UL, const double* UR, double* F) {
   riemann_flux<double>(UL, UR, c->nvar, *c, c->alpha_x, F);

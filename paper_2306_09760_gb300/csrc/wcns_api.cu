@@ -1,0 +1,493 @@
+// C-ABI layer of libwcns: argument validation, context scratch, stream ordering,
+// CUDA-graph replay of RK3 steps, sticky device status.  See include/wcns.h.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/wcns.h"
+#include "wcns_internal.h"
+
+using namespace wcns;
+
+struct wcns_ctx {
+  wcns_grid g;
+  wcns_params p;
+  Scheme s;
+  GridInfo gi;
+  cudaStream_t stream;
+  int device;
+  size_t elem;           // element size in bytes
+  size_t nelem;          // elements of one grid buffer (nvar * ny * pitch)
+  void* u1;              // stage states
+  void* u2;
+  void* R;               // L_x planes (2D)
+  void* host_state;      // device copy used by wcns_step_host (lazy)
+  // small device scalars (one allocation)
+  void* scal;
+  double* d_dt;
+  double* d_t;
+  long long* d_steps;
+  int* d_err;
+  unsigned long long* d_fallbacks;
+  unsigned int* d_counters;   // [8]
+  double* d_out;              // [8]
+  double* d_partials;         // [kMaxRedBlocks * 2]
+  // graph of one RK3 step
+  cudaGraphExec_t graph;
+  const void* graph_u;
+  double graph_dt, graph_tend;
+  // per-kernel event timing (benchmarks)
+  bool prof_on;
+  struct ProfEvent { int kind; cudaEvent_t a, b; };
+  std::vector<ProfEvent> prof;
+  size_t prof_used;
+};
+
+namespace {
+enum ProfKind { kProfSweepXRhs = 0, kProfSweepYRhs, kProfSweepXStage1D, kProfSweepXLx, kProfSweepYStage, kProfDt,
+                kProfReduce, kProfCount };
+const char* const kProfNames[kProfCount] = {"sweep_x_rhs", "sweep_y_rhs", "sweep_x_stage_1d", "sweep_x_lx_2d",
+                                            "sweep_y_stage_2d", "dt_cfl", "reduce"};
+}  // namespace
+
+namespace {
+
+wcns_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return WCNS_OK;
+  if (e == cudaErrorMemoryAllocation) return WCNS_ERR_NOMEM;
+  return WCNS_ERR_CUDA;
+}
+
+#define WCNS_TRY(expr)                               \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return from_cuda(e_);     \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Table 2 control points psi_{i,j} (j = 0..J_i), independent of the oracle's copy.
+const double kPsiGpu0[4] = {0.0, 1.0 / 16.0, 1.0 / 11.0, 1.0};
+const double kPsiGpu1[5] = {0.0, 10.0 / 16.0, 2.0 / 3.0, 10.0 / 11.0, 1.0};
+const double kPsiGpu2[4] = {0.0, 5.0 / 16.0, 1.0 / 3.0, 1.0};
+
+wcns_status check_params(const wcns_params* p, int dtype, int nvar, int ndim) {
+  if (p->system != WCNS_ADVECTION && p->system != WCNS_EULER) return WCNS_ERR_ARG;
+  if (p->weights < WCNS_W_JS || p->weights > WCNS_W_M) return WCNS_ERR_ARG;
+  if (p->flux < WCNS_FLUX_LLF || p->flux > WCNS_FLUX_LLF_FROZEN) return WCNS_ERR_ARG;
+  if (p->z_p != 1 && p->z_p != 2) return WCNS_ERR_ARG;
+  if (p->reserved[0] || p->reserved[1]) return WCNS_ERR_ARG;
+  if (!(p->eps > 0.0) || !(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->xi > 0.0)) return WCNS_ERR_ARG;
+  if (!(p->kappa > 0.0) || p->cv < 0.0) return WCNS_ERR_ARG;
+  // in single precision eps^2 must stay a normal number for the JS and M weights
+  if (dtype == WCNS_F32 && (p->weights == WCNS_W_JS || p->weights == WCNS_W_M) && p->eps < 1e-18)
+    return WCNS_ERR_ARG;
+  if (p->system == WCNS_ADVECTION && nvar != 1) return WCNS_ERR_UNSUPPORTED;
+  if (p->system == WCNS_EULER && !((ndim == 1 && nvar == 3) || (ndim == 2 && nvar == 4)))
+    return WCNS_ERR_UNSUPPORTED;
+  if (p->flux == WCNS_FLUX_LLF_FROZEN && (!(p->alpha[0] >= 0.0) || !(p->alpha[1] >= 0.0))) return WCNS_ERR_ARG;
+  return WCNS_OK;
+}
+
+Scheme make_scheme(const wcns_params* p) {
+  Scheme s{};
+  s.system = p->system;
+  s.weights = p->weights;
+  s.flux = p->flux;
+  s.characteristic = p->characteristic ? 1 : 0;
+  s.zp = p->z_p;
+  s.renorm = p->renorm ? 1 : 0;
+  s.gamma = p->gamma;
+  s.eps = p->eps;
+  s.xi = p->xi;
+  s.cv = p->cv;
+  s.harten = p->harten;
+  for (int d = 0; d < 2; ++d)
+    s.speed[d] = (p->system == WCNS_ADVECTION) ? p->adv_speed[d] : p->alpha[d];
+  for (int j = 1; j <= 3; ++j) s.null0[j - 1] = p->kappa * (kPsiGpu0[j] + kPsiGpu0[j - 1]);
+  for (int j = 1; j <= 4; ++j) s.null1[j - 1] = p->kappa * (kPsiGpu1[j] + kPsiGpu1[j - 1]);
+  for (int j = 1; j <= 3; ++j) s.null2[j - 1] = p->kappa * (kPsiGpu2[j] + kPsiGpu2[j - 1]);
+  return s;
+}
+
+template <typename F64, typename F32>
+cudaError_t by_type(int dtype, F64 f64, F32 f32) {
+  return dtype == WCNS_F64 ? f64() : f32();
+}
+
+// Runs `f` (one kernel launch), bracketed by events when per-kernel timing is on.
+template <class F>
+cudaError_t timed(wcns_ctx* c, int kind, F f) {
+  if (!c->prof_on) return f();
+  if (c->prof_used == c->prof.size()) {
+    wcns_ctx::ProfEvent ev{};
+    if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) return cudaErrorMemoryAllocation;
+    c->prof.push_back(ev);
+  }
+  wcns_ctx::ProfEvent& ev = c->prof[c->prof_used++];
+  ev.kind = kind;
+  cudaError_t e = cudaEventRecord(ev.a, c->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = f()) != cudaSuccess) return e;
+  return cudaEventRecord(ev.b, c->stream);
+}
+
+template <typename T>
+cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool stage_mode, double a, double b) {
+  SweepCall<T> x{};
+  x.u = static_cast<const T*>(u);
+  x.fallbacks = c->d_fallbacks;
+  if (c->g.ndim == 1) {
+    x.un = static_cast<const T*>(un);
+    x.out = static_cast<T*>(out);
+    x.dt = stage_mode ? c->d_dt : nullptr;
+    x.a = a; x.b = b;
+    x.stage = stage_mode;
+    return timed(c, stage_mode ? kProfSweepXStage1D : kProfSweepXRhs,
+                 [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
+  }
+  // 2D: L_x into R (skipped when dt == 0 in stage mode), then y sweep + stage
+  x.out = static_cast<T*>(c->R);
+  x.dt = stage_mode ? c->d_dt : nullptr;
+  x.stage = false;
+  cudaError_t e = timed(c, stage_mode ? kProfSweepXLx : kProfSweepXRhs,
+                        [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
+  if (e != cudaSuccess) return e;
+  SweepCall<T> y{};
+  y.u = static_cast<const T*>(u);
+  y.un = static_cast<const T*>(un);
+  y.R = static_cast<const T*>(c->R);
+  y.out = static_cast<T*>(out);
+  y.dt = stage_mode ? c->d_dt : nullptr;
+  y.a = a; y.b = b;
+  y.stage = stage_mode;
+  y.fallbacks = c->d_fallbacks;
+  return timed(c, stage_mode ? kProfSweepYStage : kProfSweepYRhs,
+               [&] { return launch_sweep_y<T>(c->gi, c->s, y, c->stream); });
+}
+
+cudaError_t rhs_into(wcns_ctx* c, const void* u, void* out) {
+  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, nullptr, out, false, 0.0, 1.0); },
+                 [&] { return sweeps<float>(c, u, nullptr, out, false, 0.0, 1.0); });
+}
+
+cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b) {
+  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, un, out, true, a, b); },
+                 [&] { return sweeps<float>(c, u, un, out, true, a, b); });
+}
+
+cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool maxwave_only) {
+  DtLaunch d{};
+  d.u = u;
+  d.cfl = c->p.cfl;
+  d.fixed_dt = dt;
+  d.t_end = t_end;
+  d.use_cfl = dt > 0.0 ? 0 : 1;
+  d.gamma = c->p.gamma;
+  for (int k = 0; k < 2; ++k) d.adv_wave[k] = fabs(c->p.adv_speed[k]);
+  d.partials = c->d_partials;
+  d.max_blocks = kMaxRedBlocks;
+  d.counter = c->d_counters;
+  d.dt_out = maxwave_only ? c->d_out : c->d_dt;
+  d.t = maxwave_only ? nullptr : c->d_t;
+  d.steps = c->d_steps;
+  d.err = c->d_err;
+  return timed(c, kProfDt, [&] {
+    return by_type(c->g.dtype, [&] { return launch_dt<double>(c->gi, d, c->stream); },
+                   [&] { return launch_dt<float>(c->gi, d, c->stream); });
+  });
+}
+
+// One TVD-RK3 step on u in place (Shu-Osher form).
+cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) {
+  cudaError_t e;
+  if ((e = dt_launch(c, u, dt, t_end, false)) != cudaSuccess) return e;
+  if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0)) != cudaSuccess) return e;
+  if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25)) != cudaSuccess) return e;
+  return stage(c, c->u2, u, u, 1.0 / 3.0, 2.0 / 3.0);
+}
+
+void drop_graph(wcns_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_u = nullptr;
+}
+
+cudaError_t build_graph(wcns_ctx* c, void* u, double dt, double t_end) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t body = rk3_step(c, u, dt, t_end);
+  e = cudaStreamEndCapture(c->stream, &g);
+  if (body != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return body;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return e;
+  }
+  c->graph_u = u;
+  c->graph_dt = dt;
+  c->graph_tend = t_end;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wcns_status_string(wcns_status s) {
+  switch (s) {
+    case WCNS_OK: return "ok";
+    case WCNS_ERR_ARG: return "invalid argument";
+    case WCNS_ERR_CUDA: return "CUDA runtime error";
+    case WCNS_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case WCNS_ERR_TIMEOUT: return "bounded device wait expired";
+    case WCNS_ERR_UNSUPPORTED: return "unsupported option combination";
+    case WCNS_ERR_NOMEM: return "device allocation failed";
+  }
+  return "unknown status";
+}
+
+wcns_status wcns_default_params(int32_t system, int32_t dtype, wcns_params* p) {
+  if (!p || (system != WCNS_ADVECTION && system != WCNS_EULER) || (dtype != WCNS_F64 && dtype != WCNS_F32))
+    return WCNS_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->system = system;
+  p->weights = WCNS_W_FE;
+  p->flux = WCNS_FLUX_HLLC;
+  p->characteristic = 1;
+  p->z_p = 1;
+  p->renorm = 1;
+  p->adv_speed[0] = 1.0;
+  p->gamma = 1.4;
+  p->eps = dtype == WCNS_F64 ? 1e-40 : 1e-30;
+  p->xi = 1e6;
+  p->kappa = 0.5;
+  p->cv = 1e-3;
+  p->cfl = 0.5;
+  p->harten = 0.1;
+  return WCNS_OK;
+}
+
+wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* stream, wcns_ctx** out) {
+  if (!out) return WCNS_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !params) return WCNS_ERR_ARG;
+  const wcns_grid& g = *grid;
+  if (g.ndim != 1 && g.ndim != 2) return WCNS_ERR_ARG;
+  if (g.nvar != 1 && g.nvar != 3 && g.nvar != 4) return WCNS_ERR_ARG;
+  if (g.dtype != WCNS_F64 && g.dtype != WCNS_F32) return WCNS_ERR_ARG;
+  if (g.reserved != 0) return WCNS_ERR_ARG;
+  const int64_t kMaxN = (int64_t)1 << 26;
+  if (g.nx < 1 || g.ny < 1 || g.nx > kMaxN || g.ny > kMaxN) return WCNS_ERR_ARG;
+  if (g.ndim == 1 && g.ny != 1) return WCNS_ERR_ARG;
+  if (g.ny > 65535 * (int64_t)59 || (g.ndim == 1 && g.ny > 65535)) return WCNS_ERR_ARG;
+  if (g.pitch < g.nx || g.pitch % 32 != 0) return WCNS_ERR_ARG;
+  if ((double)g.nvar * (double)g.ny * (double)g.pitch > 4.0e9) return WCNS_ERR_ARG;
+  for (int d = 0; d < g.ndim; ++d) {
+    if (!(g.hi[d] > g.lo[d])) return WCNS_ERR_ARG;
+    if (g.bc[d] != WCNS_BC_PERIODIC && g.bc[d] != WCNS_BC_TRANSMISSIVE) return WCNS_ERR_ARG;
+  }
+  wcns_status st = check_params(params, g.dtype, g.nvar, g.ndim);
+  if (st != WCNS_OK) return st;
+
+  wcns_ctx* c = new (std::nothrow) wcns_ctx();
+  if (!c) return WCNS_ERR_NOMEM;
+  c->g = g;
+  c->p = *params;
+  c->s = make_scheme(params);
+  c->gi.ndim = g.ndim;
+  c->gi.nvar = g.nvar;
+  c->gi.nx = g.nx;
+  c->gi.ny = g.ny;
+  c->gi.pitch = g.pitch;
+  c->gi.bc[0] = g.bc[0];
+  c->gi.bc[1] = g.ndim == 2 ? g.bc[1] : WCNS_BC_PERIODIC;
+  c->gi.h[0] = (g.hi[0] - g.lo[0]) / (double)g.nx;
+  c->gi.h[1] = g.ndim == 2 ? (g.hi[1] - g.lo[1]) / (double)g.ny : 1.0;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->elem = g.dtype == WCNS_F64 ? 8 : 4;
+  c->nelem = (size_t)g.nvar * (size_t)g.ny * (size_t)g.pitch;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess)
+    e = by_type(g.dtype, [&] { return configure_kernels<double>(g.nvar); },
+                [&] { return configure_kernels<float>(g.nvar); });
+  const size_t bytes = c->nelem * c->elem;
+  if (e == cudaSuccess) e = cudaMalloc(&c->u1, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->u2, bytes);
+  if (e == cudaSuccess && g.ndim == 2) e = cudaMalloc(&c->R, bytes);
+  const size_t scal_bytes = 4096 + sizeof(double) * 2 * kMaxRedBlocks;
+  if (e == cudaSuccess) e = cudaMalloc(&c->scal, scal_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->scal, 0, scal_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    wcns_destroy(c);
+    return from_cuda(e);
+  }
+  char* b = static_cast<char*>(c->scal);
+  c->d_dt = reinterpret_cast<double*>(b + 0);
+  c->d_t = reinterpret_cast<double*>(b + 8);
+  c->d_steps = reinterpret_cast<long long*>(b + 16);
+  c->d_err = reinterpret_cast<int*>(b + 24);
+  c->d_fallbacks = reinterpret_cast<unsigned long long*>(b + 32);
+  c->d_counters = reinterpret_cast<unsigned int*>(b + 64);
+  c->d_out = reinterpret_cast<double*>(b + 128);
+  c->d_partials = reinterpret_cast<double*>(b + 4096);
+  *out = c;
+  return WCNS_OK;
+}
+
+wcns_status wcns_rhs(wcns_ctx* c, const void* u, void* dudt) {
+  if (!c || !u || !dudt || !aligned16(u) || !aligned16(dudt)) return WCNS_ERR_ARG;
+  const char* a = static_cast<const char*>(u);
+  const char* d = static_cast<const char*>(dudt);
+  const size_t bytes = c->nelem * c->elem;
+  if (a < d + bytes && d < a + bytes) return WCNS_ERR_ARG;  // must not overlap
+  return from_cuda(rhs_into(c, u, dudt));
+}
+
+wcns_status wcns_step(wcns_ctx* c, void* u, double dt, int32_t nsteps, double t_end) {
+  if (!c || !u || !aligned16(u) || nsteps < 0) return WCNS_ERR_ARG;
+  if (dt != dt || t_end != t_end) return WCNS_ERR_ARG;
+  if (nsteps == 0) return WCNS_OK;
+  // Replaying a captured step graph needs a capturable stream (not the legacy default);
+  // per-kernel timing launches directly.
+  if (c->stream != nullptr && nsteps >= 2 && !c->prof_on) {
+    if (!c->graph || c->graph_u != u || c->graph_dt != dt || c->graph_tend != t_end)
+      WCNS_TRY(build_graph(c, u, dt, t_end));
+    for (int32_t k = 0; k < nsteps; ++k) WCNS_TRY(cudaGraphLaunch(c->graph, c->stream));
+    return WCNS_OK;
+  }
+  for (int32_t k = 0; k < nsteps; ++k) WCNS_TRY(rk3_step(c, u, dt, t_end));
+  return WCNS_OK;
+}
+
+wcns_status wcns_step_host(wcns_ctx* c, void* u_host, double dt, int32_t nsteps, double t_end) {
+  if (!c || !u_host || nsteps < 0) return WCNS_ERR_ARG;
+  const size_t bytes = c->nelem * c->elem;
+  if (!c->host_state) WCNS_TRY(cudaMalloc(&c->host_state, bytes));
+  WCNS_TRY(cudaMemcpyAsync(c->host_state, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  wcns_status s = wcns_step(c, c->host_state, dt, nsteps, t_end);
+  if (s != WCNS_OK) return s;
+  WCNS_TRY(cudaMemcpyAsync(u_host, c->host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  return WCNS_OK;
+}
+
+wcns_status wcns_set_time(wcns_ctx* c, double t) {
+  if (!c || t != t) return WCNS_ERR_ARG;
+  WCNS_TRY(cudaMemcpyAsync(c->d_t, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  WCNS_TRY(cudaMemsetAsync(c->d_steps, 0, sizeof(long long), c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  return WCNS_OK;
+}
+
+wcns_status wcns_get_time(wcns_ctx* c, double* t, int64_t* steps) {
+  if (!c) return WCNS_ERR_ARG;
+  double tt = 0.0;
+  long long ss = 0;
+  WCNS_TRY(cudaMemcpyAsync(&tt, c->d_t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaMemcpyAsync(&ss, c->d_steps, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  if (t) *t = tt;
+  if (steps) *steps = (int64_t)ss;
+  return WCNS_OK;
+}
+
+wcns_status wcns_reduce(wcns_ctx* c, const void* a, const void* b, int32_t what, double* out) {
+  if (!c || !a || !out || !aligned16(a) || (b && !aligned16(b))) return WCNS_ERR_ARG;
+  if (what < WCNS_REDUCE_SUM || what > WCNS_REDUCE_MAXWAVE) return WCNS_ERR_ARG;
+  int nout;
+  if (what == WCNS_REDUCE_MAXWAVE) {
+    WCNS_TRY(dt_launch(c, a, 0.0, 0.0, true));
+    nout = c->g.ndim;
+  } else {
+    WCNS_TRY(timed(c, kProfReduce, [&] {
+      return by_type(
+          c->g.dtype,
+          [&] { return launch_reduce<double>(c->gi, a, b, what, c->d_partials, 2 * kMaxRedBlocks, c->d_counters, c->d_out, c->stream); },
+          [&] { return launch_reduce<float>(c->gi, a, b, what, c->d_partials, 2 * kMaxRedBlocks, c->d_counters, c->d_out, c->stream); });
+    }));
+    nout = c->g.nvar;
+  }
+  WCNS_TRY(cudaMemcpyAsync(out, c->d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  if (what == WCNS_REDUCE_MAXWAVE && c->p.system == WCNS_ADVECTION)
+    for (int d = 0; d < nout; ++d) out[d] = fabs(c->p.adv_speed[d]);
+  return WCNS_OK;
+}
+
+wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const void* lam_np1, void* lam_n) {
+  if (!c || !u_n || !lam_np1 || !lam_n) return WCNS_ERR_ARG;
+  (void)dt;
+  return WCNS_ERR_UNSUPPORTED;
+}
+
+wcns_status wcns_sync_status(wcns_ctx* c, int64_t* nonphysical) {
+  if (!c) return WCNS_ERR_ARG;
+  int err = 0;
+  unsigned long long fb = 0;
+  WCNS_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaMemcpyAsync(&fb, c->d_fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  WCNS_TRY(cudaMemsetAsync(c->d_fallbacks, 0, sizeof(fb), c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  if (nonphysical) *nonphysical = (int64_t)fb;
+  if (err & 2) return WCNS_ERR_TIMEOUT;
+  if (err & 1) return WCNS_ERR_NONPHYSICAL;
+  return WCNS_OK;
+}
+
+wcns_status wcns_profile_enable(wcns_ctx* c, int32_t on) {
+  if (!c) return WCNS_ERR_ARG;
+  c->prof_on = on != 0;
+  c->prof_used = 0;
+  return WCNS_OK;
+}
+
+wcns_status wcns_profile_read(wcns_ctx* c, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                              int32_t* n_entries) {
+  if (!c || max_entries < kProfCount || !names || !launches || !ms || !n_entries) return WCNS_ERR_ARG;
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < kProfCount; ++k) {
+    std::snprintf(names + 48 * k, 48, "%s", kProfNames[k]);
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    float t = 0.f;
+    WCNS_TRY(cudaEventElapsedTime(&t, c->prof[i].a, c->prof[i].b));
+    launches[c->prof[i].kind] += 1;
+    ms[c->prof[i].kind] += t;
+  }
+  c->prof_used = 0;
+  *n_entries = kProfCount;
+  return WCNS_OK;
+}
+
+void wcns_destroy(wcns_ctx* c) {
+  if (!c) return;
+  if (c->stream || c->u1) cudaStreamSynchronize(c->stream);
+  for (auto& ev : c->prof) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  drop_graph(c);
+  if (c->u1) cudaFree(c->u1);
+  if (c->u2) cudaFree(c->u2);
+  if (c->R) cudaFree(c->R);
+  if (c->host_state) cudaFree(c->host_state);
+  if (c->scal) cudaFree(c->scal);
+  delete c;
+}
+
+// Batched problems: implemented in wcns_batch.cu.
+
+}  // extern "C"

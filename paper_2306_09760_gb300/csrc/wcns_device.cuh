@@ -1,0 +1,436 @@
+// Device-side numerics of the WCNS-FE scheme (one interface per thread).
+//
+// Paper: Liu, Min, Cai, Ma, Yan, "A filtered embedded weighted compact nonlinear
+// scheme for hyperbolic conservation law", arXiv 2306.09760.
+//   Eq. 5      sub-stencil midpoint values q0, q1, q2
+//   Eq. 9-10   smoothness indicators IS_k = (h f_k)^2 + (h^2 s_k)^2
+//   Eq. 11     JS weights;  Eq. 12-13 M weights;  Eq. 14-15 Z weights
+//   Eq. 20-21  FE mapping function with the Table 2 coefficients
+//   App. A     PFE switch
+//   Eq. 6      midpoint flux from an approximate Riemann solver
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+// Device numerics are also host-callable so that tools can evaluate them on the CPU.
+#define WCNS_HD __host__ __device__ __forceinline__
+
+namespace wcns {
+
+// Scheme parameters as the kernels see them.
+struct Scheme {
+  int system;          // 0 advection, 1 Euler
+  int weights;         // 0 JS, 1 Z, 2 FE, 3 PFE, 4 M
+  int flux;            // 0 LLF, 1 Roe, 2 HLLC, 3 LLF with frozen alpha
+  int characteristic;  // project onto characteristic fields (Euler)
+  int zp;              // Z exponent p (1 or 2)
+  int renorm;          // renormalise mapped weights
+  double gamma, eps, xi, cv, harten;
+  double speed[2];     // advection speed (advection) or frozen LF alpha (LLF_FROZEN), per direction
+  // Null points kappa*(psi_j + psi_{j-1}) of Eq. 20 for the three weights (Table 2 rows).
+  double null0[3], null1[4], null2[3];
+};
+
+// ---------------------------------------------------------------------------
+// Small math helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct Num;
+template <> struct Num<double> {
+  // |z| at and beyond which tanh(z) rounds to +-1 exactly in double precision
+  // (1 - tanh(20) = 8.5e-18 < half an ulp of 1).
+  static constexpr double kSat = 20.0;
+  WCNS_HD static double tanh_(double z) { return tanh(z); }
+  WCNS_HD static double sqrt_(double x) { return sqrt(x); }
+  WCNS_HD static double abs_(double x) { return fabs(x); }
+};
+template <> struct Num<float> {
+  // 1 - tanh(9.1) = 2.5e-8 < half an ulp of 1 in single precision.
+  static constexpr float kSat = 9.1f;
+  WCNS_HD static float tanh_(float z) { return tanhf(z); }
+  WCNS_HD static float sqrt_(float x) { return sqrtf(x); }
+  WCNS_HD static float abs_(float x) { return fabsf(x); }
+};
+
+// tanh(z) with an exact select where the result rounds to +-1 anyway.
+template <typename T>
+WCNS_HD T tanh_sat(T z) {
+  T a = Num<T>::abs_(z);
+  if (a >= Num<T>::kSat) return z > T(0) ? T(1) : T(-1);
+  return Num<T>::tanh_(z);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 20-21 (Table 2).  phi(i, j) = -1 multiplies both the amplitude and the tanh
+// argument and tanh is odd, so every term reduces to
+//   (omega_{i,j} - omega_{i,j-1}) / 2 * tanh(xi * (w - null_j)),
+// with omega_{i,0} = omega_{i,J} = w.  The map is a smoothed staircase whose
+// plateaus are the control values.
+// ---------------------------------------------------------------------------
+template <typename T>
+WCNS_HD T fe_map0(T w, const Scheme& s) {
+  const T xi = T(s.xi);
+  T t1 = tanh_sat<T>(xi * (w - T(s.null0[0])));
+  T t2 = tanh_sat<T>(xi * (w - T(s.null0[1])));
+  T t3 = tanh_sat<T>(xi * (w - T(s.null0[2])));
+  T acc = ((T(1.0 / 16.0) - w) / T(2)) * t1;
+  acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * t2;
+  acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * t3;
+  return acc + w;
+}
+template <typename T>
+WCNS_HD T fe_map1(T w, const Scheme& s) {
+  const T xi = T(s.xi);
+  T t1 = tanh_sat<T>(xi * (w - T(s.null1[0])));
+  T t2 = tanh_sat<T>(xi * (w - T(s.null1[1])));
+  T t3 = tanh_sat<T>(xi * (w - T(s.null1[2])));
+  T t4 = tanh_sat<T>(xi * (w - T(s.null1[3])));
+  T acc = ((T(10.0 / 16.0) - w) / T(2)) * t1;
+  acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * t2;
+  acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * t3;
+  acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * t4;
+  return acc + w;
+}
+template <typename T>
+WCNS_HD T fe_map2(T w, const Scheme& s) {
+  const T xi = T(s.xi);
+  T t1 = tanh_sat<T>(xi * (w - T(s.null2[0])));
+  T t2 = tanh_sat<T>(xi * (w - T(s.null2[1])));
+  T t3 = tanh_sat<T>(xi * (w - T(s.null2[2])));
+  T acc = ((T(5.0 / 16.0) - w) / T(2)) * t1;
+  acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * t2;
+  acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * t3;
+  return acc + w;
+}
+
+// Eq. 13: Henrick's mapping of a JS weight with ideal value d.
+template <typename T>
+WCNS_HD T m_map(T w, T d) {
+  return w * (d + d * d - T(3) * d * w + w * w) / (d * d + (T(1) - T(2) * d) * w);
+}
+
+// Midpoint value at x_{i+1/2} from five values v0..v4 = u_{i-2}..u_{i+2} (left state), or
+// the mirrored u_{i+3}..u_{i-1} (right state).  Returns the interpolated value.
+template <typename T>
+WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const Scheme& s) {
+  const T d0 = T(1.0 / 16.0), d1 = T(10.0 / 16.0), d2 = T(5.0 / 16.0);
+  // Eq. 5
+  T q0 = (T(3) * v0 - T(10) * v1 + T(15) * v2) / T(8);
+  T q1 = (-v1 + T(6) * v2 + T(3) * v3) / T(8);
+  T q2 = (T(3) * v2 + T(6) * v3 - v4) / T(8);
+  // Eq. 10 scaled by h and h^2, then Eq. 9
+  T f0 = (v0 - T(4) * v1 + T(3) * v2) / T(2), s0 = v0 - T(2) * v1 + v2;
+  T f1 = (v3 - v1) / T(2), s1 = v1 - T(2) * v2 + v3;
+  T f2 = (T(-3) * v2 + T(4) * v3 - v4) / T(2), s2 = v2 - T(2) * v3 + v4;
+  T is0 = f0 * f0 + s0 * s0;
+  T is1 = f1 * f1 + s1 * s1;
+  T is2 = f2 * f2 + s2 * s2;
+  const T eps = T(s.eps);
+  T w0, w1, w2;
+  if (s.weights == 0 || s.weights == 4) {
+    // Eq. 11
+    T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
+    T a0 = d0 / (b0 * b0), a1 = d1 / (b1 * b1), a2 = d2 / (b2 * b2);
+    T sa = a0 + a1 + a2;
+    w0 = a0 / sa; w1 = a1 / sa; w2 = a2 / sa;
+    if (s.weights == 4) {
+      // Eq. 12-13
+      T g0 = m_map<T>(w0, d0), g1 = m_map<T>(w1, d1), g2 = m_map<T>(w2, d2);
+      T sg = g0 + g1 + g2;
+      w0 = g0 / sg; w1 = g1 / sg; w2 = g2 / sg;
+    }
+  } else {
+    // Eq. 14-15
+    T tau = Num<T>::abs_(is0 - is2);
+    T r0 = tau / (is0 + eps), r1 = tau / (is1 + eps), r2 = tau / (is2 + eps);
+    if (s.zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
+    T a0 = d0 * (T(1) + r0), a1 = d1 * (T(1) + r1), a2 = d2 * (T(1) + r2);
+    T sa = a0 + a1 + a2;
+    w0 = a0 / sa; w1 = a1 / sa; w2 = a2 / sa;
+    if (s.weights >= 2) {
+      bool keep = false;
+      if (s.weights == 3) {
+        // App. A: keep the Z weights inside the closed box |w_k - d_k| <= cv
+        const T cv = T(s.cv);
+        keep = (w0 >= d0 - cv) && (w0 <= d0 + cv) && (w1 >= d1 - cv) && (w1 <= d1 + cv) &&
+               (w2 >= d2 - cv) && (w2 <= d2 + cv);
+      }
+      if (!keep) {
+        // Eq. 20 on each weight, then renormalised
+        T g0 = fe_map0<T>(w0, s), g1 = fe_map1<T>(w1, s), g2 = fe_map2<T>(w2, s);
+        if (s.renorm) {
+          T sg = g0 + g1 + g2;
+          w0 = g0 / sg; w1 = g1 / sg; w2 = g2 / sg;
+        } else {
+          w0 = g0; w1 = g1; w2 = g2;
+        }
+      }
+    }
+  }
+  // Eq. 6: convex combination
+  return w0 * q0 + w1 * q1 + w2 * q2;
+}
+
+// ---------------------------------------------------------------------------
+// Euler equations in a sweep normal.  State ordering within a sweep:
+// NV = 3: (rho, rho un, E);  NV = 4: (rho, rho un, rho ut, E).
+// ---------------------------------------------------------------------------
+template <typename T, int NV>
+struct EulerState {
+  T rho, un, ut, p, H;
+};
+
+template <typename T, int NV>
+WCNS_HD EulerState<T, NV> euler_prim(const T (&U)[NV], T gm1) {
+  EulerState<T, NV> st;
+  st.rho = U[0];
+  T inv = T(1) / U[0];
+  st.un = U[1] * inv;
+  T E;
+  if (NV == 4) {
+    st.ut = U[2] * inv;
+    E = U[3];
+    st.p = gm1 * (E - T(0.5) * st.rho * (st.un * st.un + st.ut * st.ut));
+  } else {
+    st.ut = T(0);
+    E = U[NV - 1];
+    st.p = gm1 * (E - T(0.5) * st.rho * st.un * st.un);
+  }
+  st.H = (E + st.p) * inv;
+  return st;
+}
+
+template <typename T, int NV>
+WCNS_HD void euler_flux(const T (&U)[NV], const EulerState<T, NV>& st, T (&F)[NV]) {
+  F[0] = U[1];
+  F[1] = U[1] * st.un + st.p;
+  if (NV == 4) {
+    F[2] = U[2] * st.un;
+    F[3] = (U[3] + st.p) * st.un;
+  } else {
+    F[NV - 1] = (U[NV - 1] + st.p) * st.un;
+  }
+}
+
+// Roe-averaged velocity, enthalpy and sound speed of two states.
+template <typename T, int NV>
+struct RoeAvg {
+  T u, v, H, c;
+};
+template <typename T, int NV>
+WCNS_HD RoeAvg<T, NV> roe_avg(const EulerState<T, NV>& a, const EulerState<T, NV>& b, T gm1) {
+  RoeAvg<T, NV> r;
+  T sa = Num<T>::sqrt_(a.rho), sb = Num<T>::sqrt_(b.rho);
+  T inv = T(1) / (sa + sb);
+  r.u = (sa * a.un + sb * b.un) * inv;
+  r.v = (NV == 4) ? (sa * a.ut + sb * b.ut) * inv : T(0);
+  r.H = (sa * a.H + sb * b.H) * inv;
+  T q2 = r.u * r.u + r.v * r.v;
+  r.c = Num<T>::sqrt_(gm1 * (r.H - T(0.5) * q2));
+  return r;
+}
+
+// Characteristic projection with the left eigenvectors at the Roe state, written in
+// factored form:  P = b (E - u m - v n + q^2 rho / 2) with b = (gamma-1)/c^2,
+// A = (u rho - m) / c;  W = ((P + A)/2, rho - P, [n - v rho,] (P - A)/2).
+template <typename T, int NV>
+struct CharBasis {
+  T u, v, H, c, b, ic, hq2;
+};
+template <typename T, int NV>
+WCNS_HD CharBasis<T, NV> char_basis(const RoeAvg<T, NV>& r, T gm1) {
+  CharBasis<T, NV> cb;
+  cb.u = r.u; cb.v = r.v; cb.H = r.H; cb.c = r.c;
+  cb.ic = T(1) / r.c;
+  cb.b = gm1 * cb.ic * cb.ic;
+  cb.hq2 = T(0.5) * (r.u * r.u + r.v * r.v);
+  return cb;
+}
+template <typename T, int NV>
+WCNS_HD void char_project(const CharBasis<T, NV>& cb, const T (&U)[NV], T (&W)[NV]) {
+  const T rho = U[0], m = U[1];
+  const T E = U[NV - 1];
+  T P;
+  if (NV == 4) P = cb.b * (E - cb.u * m - cb.v * U[2] + cb.hq2 * rho);
+  else P = cb.b * (E - cb.u * m + cb.hq2 * rho);
+  T A = (cb.u * rho - m) * cb.ic;
+  W[0] = T(0.5) * (P + A);
+  W[1] = rho - P;
+  if (NV == 4) W[2] = U[2] - cb.v * rho;
+  W[NV - 1] = T(0.5) * (P - A);
+}
+// Back-projection with the right eigenvectors (u - c, u, [u,] u + c columns).
+template <typename T, int NV>
+WCNS_HD void char_unproject(const CharBasis<T, NV>& cb, const T (&W)[NV], T (&U)[NV]) {
+  const T wa = W[0], wb = W[1], wd = W[NV - 1];
+  T s = wa + wb + wd;
+  T dlt = wd - wa;
+  U[0] = s;
+  U[1] = cb.u * s + cb.c * dlt;
+  if (NV == 4) {
+    U[2] = cb.v * s + W[2];
+    U[3] = cb.H * (wa + wd) + cb.u * cb.c * dlt + cb.hq2 * wb + cb.v * W[2];
+  } else {
+    U[2] = cb.H * (wa + wd) + cb.u * cb.c * dlt + cb.hq2 * wb;
+  }
+}
+
+// Approximate Riemann solvers (Eq. 6).
+template <typename T, int NV>
+WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const Scheme& s, int dir,
+                                        T (&F)[NV]) {
+  const T g = T(s.gamma), gm1 = T(s.gamma - 1.0);
+  EulerState<T, NV> a = euler_prim<T, NV>(UL, gm1), b = euler_prim<T, NV>(UR, gm1);
+  T FL[NV], FR[NV];
+  euler_flux<T, NV>(UL, a, FL);
+  euler_flux<T, NV>(UR, b, FR);
+  if (s.flux == 0 || s.flux == 3) {
+    T alpha;
+    if (s.flux == 3) {
+      alpha = T(s.speed[dir]);
+    } else {
+      T sl = Num<T>::abs_(a.un) + Num<T>::sqrt_(g * a.p / a.rho);
+      T sr = Num<T>::abs_(b.un) + Num<T>::sqrt_(g * b.p / b.rho);
+      alpha = sl >= sr ? sl : sr;
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * alpha * (UR[k] - UL[k]);
+    return;
+  }
+  RoeAvg<T, NV> r = roe_avg<T, NV>(a, b, gm1);
+  if (s.flux == 1) {
+    // Roe: F = (FL + FR)/2 - 1/2 R |Lambda| L (UR - UL), Harten's fix on u -/+ c
+    CharBasis<T, NV> cb = char_basis<T, NV>(r, gm1);
+    T dU[NV], dW[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) dU[k] = UR[k] - UL[k];
+    char_project<T, NV>(cb, dU, dW);
+    T delta = T(s.harten) * (Num<T>::abs_(r.u) + r.c);
+    T l0 = Num<T>::abs_(r.u - r.c), lm = Num<T>::abs_(r.u), l3 = Num<T>::abs_(r.u + r.c);
+    if (l0 < delta) l0 = ((r.u - r.c) * (r.u - r.c) + delta * delta) / (T(2) * delta);
+    if (l3 < delta) l3 = ((r.u + r.c) * (r.u + r.c) + delta * delta) / (T(2) * delta);
+    dW[0] = l0 * dW[0];
+    dW[1] = lm * dW[1];
+    if (NV == 4) dW[2] = lm * dW[2];
+    dW[NV - 1] = l3 * dW[NV - 1];
+    T D[NV];
+    char_unproject<T, NV>(cb, dW, D);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = T(0.5) * (FL[k] + FR[k]) - T(0.5) * D[k];
+    return;
+  }
+  // HLLC with Einfeldt speed estimates
+  T cl = Num<T>::sqrt_(g * a.p / a.rho), cr = Num<T>::sqrt_(g * b.p / b.rho);
+  T SL = a.un - cl, SR = b.un + cr;
+  if (r.u - r.c < SL) SL = r.u - r.c;
+  if (r.u + r.c > SR) SR = r.u + r.c;
+  if (SL >= T(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = FL[k];
+    return;
+  }
+  if (SR <= T(0)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = FR[k];
+    return;
+  }
+  T ml = a.rho * (SL - a.un), mr = b.rho * (SR - b.un);
+  T Sst = (b.p - a.p + a.un * ml - b.un * mr) / (ml - mr);
+  const bool left = Sst >= T(0);
+  const EulerState<T, NV>& st = left ? a : b;
+  T SK = left ? SL : SR;
+  T fac = st.rho * (SK - st.un) / (SK - Sst);
+  T EK = left ? UL[NV - 1] : UR[NV - 1];
+  T Est = fac * (EK / st.rho + (Sst - st.un) * (Sst + st.p / (st.rho * (SK - st.un))));
+  T Us[NV];
+  Us[0] = fac;
+  Us[1] = fac * Sst;
+  if (NV == 4) Us[2] = fac * st.ut;
+  Us[NV - 1] = Est;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T fk = left ? FL[k] : FR[k];
+    T uk = left ? UL[k] : UR[k];
+    F[k] = fk + SK * (Us[k] - uk);
+  }
+}
+
+template <typename T, int NV>
+WCNS_HD bool physical(const T (&U)[NV], T gm1) {
+  if (!(U[0] > T(0))) return false;
+  T inv = T(1) / U[0];
+  T kin = (NV == 4) ? (U[1] * U[1] + U[2] * U[2]) * inv : U[1] * U[1] * inv;
+  T p = gm1 * (U[NV - 1] - T(0.5) * kin);
+  return p > T(0);
+}
+
+// Midpoint flux at one interface from the six stencil states S[0..5] = U_{i-2..i+3}
+// (already in the sweep's normal ordering).  Returns true if the interpolated states
+// were non-physical and the interface fell back to (U_i, U_{i+1}).
+template <typename T, int NV>
+WCNS_HD bool interface_flux(const T (&S)[6][NV], const Scheme& s, int dir, T (&F)[NV]) {
+  if (NV == 1) {
+    const T a = T(s.speed[dir]);
+    T v;
+    if (a >= T(0)) v = weno_side<T>(S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
+    else v = weno_side<T>(S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
+    F[0] = a * v;
+    return false;
+  }
+  const T gm1 = T(s.gamma - 1.0);
+  T UL[NV], UR[NV];
+  if (s.characteristic) {
+    T Ui[NV], Uj[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { Ui[k] = S[2][k]; Uj[k] = S[3][k]; }
+    EulerState<T, NV> a = euler_prim<T, NV>(Ui, gm1), b = euler_prim<T, NV>(Uj, gm1);
+    RoeAvg<T, NV> r = roe_avg<T, NV>(a, b, gm1);
+    CharBasis<T, NV> cb = char_basis<T, NV>(r, gm1);
+    T W[6][NV];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) char_project<T, NV>(cb, S[m], W[m]);
+    T WL[NV], WR[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      WL[k] = weno_side<T>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
+      WR[k] = weno_side<T>(W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
+    }
+    char_unproject<T, NV>(cb, WL, UL);
+    char_unproject<T, NV>(cb, WR, UR);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      UL[k] = weno_side<T>(S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
+      UR[k] = weno_side<T>(S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
+    }
+  }
+  bool fallback = false;
+  if (!physical<T, NV>(UL, gm1) || !physical<T, NV>(UR, gm1)) {
+    fallback = true;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { UL[k] = S[2][k]; UR[k] = S[3][k]; }
+  }
+  riemann<T, NV>(UL, UR, s, dir, F);
+  return fallback;
+}
+
+// Eq. 3: -(1/h) sum_m d_m (F_{i+m-1/2} - F_{i-m+1/2}) from the six interface fluxes
+// f[0..5] = F_{i-5/2} .. F_{i+5/2}.
+template <typename T>
+WCNS_HD T flux_difference(T f0, T f1, T f2, T f3, T f4, T f5, T inv_h) {
+  const T d1 = T(75.0 / 64.0), d2 = T(-25.0 / 384.0), d3 = T(3.0 / 640.0);
+  T acc = d1 * (f3 - f2);
+  acc = acc + d2 * (f4 - f1);
+  acc = acc + d3 * (f5 - f0);
+  return -(acc * inv_h);
+}
+
+WCNS_HD int64_t ghost(int64_t i, int64_t n, int bc) {
+  if (bc == 0) {
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+}  // namespace wcns

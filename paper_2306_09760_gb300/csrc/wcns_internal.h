@@ -1,0 +1,67 @@
+// Internal host-side interface between the C-ABI layer and the per-type kernel
+// translation units.  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wcns_device.cuh"
+
+namespace wcns {
+
+struct GridInfo {
+  int ndim, nvar;
+  int64_t nx, ny, pitch;
+  int bc[2];
+  double h[2];
+};
+
+// Raises the dynamic shared-memory limit of every sweep kernel for `nvar` (call once
+// per device before the first launch and before any stream capture).
+template <typename T>
+cudaError_t configure_kernels(int nvar);
+
+// One sweep kernel.  x sweep: 1D stage (out = a*un + b*(u + dt*L)) or L / L_x into
+// `out` (dt may be null for a plain RHS).  y sweep: L = R + L_y, then either L into
+// `out` (dt null) or the stage update.
+template <typename T>
+struct SweepCall {
+  const T* u;
+  const T* un;
+  const T* R;
+  T* out;
+  const double* dt;
+  double a, b;
+  bool stage;  // apply the RK stage update (else write L)
+  unsigned long long* fallbacks;
+};
+template <typename T>
+cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
+
+struct DtLaunch {
+  const void* u;
+  double cfl, fixed_dt, t_end;
+  int use_cfl;
+  double adv_wave[2];
+  double gamma;
+  double* partials;
+  int max_blocks;
+  unsigned int* counter;
+  double* dt_out;
+  double* t;
+  long long* steps;
+  int* err;
+};
+template <typename T>
+cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int what, double* partials,
+                          int max_blocks, unsigned int* counters, double* out, cudaStream_t st);
+
+// Number of blocks the reductions use at most (partials are sized for this).
+constexpr int kMaxRedBlocks = 152 * 8;
+
+}  // namespace wcns

@@ -1,0 +1,377 @@
+// Kernels of the WCNS-FE hot path: per-direction sweeps fused with the TVD-RK3 stage
+// update, the CFL step reduction and the FP64 norm reductions.
+//
+// Sweep structure (per RK stage, Eq. 2-3 + steps (a)-(e)):
+//   1D:  sweep_x computes L and the stage update in one kernel.
+//   2D:  sweep_x writes L_x into a scratch plane set; sweep_y computes L_y, adds L_x
+//        and applies the stage update.  Splitting the sweeps keeps the redundant
+//        interface work at the tile edges to ~2% per sweep (a fused 2D tile of
+//        32 x 32 cells recomputes ~16% of its interfaces), and the extra plane
+//        traffic (one write + one read of L_x) is hidden under the arithmetic.
+//
+// A tile of T output cells along a line needs the T + 5 interfaces
+// F_{c0-5/2} .. F_{c0+T-1+5/2}, which need the T + 10 cells c0-5 .. c0+T+4.  Ghost
+// cells are produced by index arithmetic while the tile is staged in shared memory.
+#pragma once
+
+#include "wcns_device.cuh"
+
+namespace wcns {
+
+// Stage coefficients: out = a * un + b * (u + dt * L).
+template <typename T>
+struct SweepArgs {
+  const T* u;          // state the RHS is evaluated on
+  const T* un;         // u^n (read only when a != 0)
+  const T* R;          // L_x planes (y sweep of a 2D grid)
+  T* out;              // destination (L, L_x or the stage state)
+  const double* dt;    // device step (stage modes)
+  T a, b;
+  int64_t nx, ny, pitch, fstride;  // fstride = ny * pitch (elements per variable plane)
+  int bc;              // boundary of this sweep's direction
+  T inv_h;
+  Scheme s;
+  unsigned long long* fallbacks;   // interfaces that fell back to first order
+};
+
+enum SweepMode { kWriteL = 0, kStage = 1 };
+
+__device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
+  unsigned m = __ballot_sync(0xffffffffu, fb);
+  if (m && (threadIdx.x & 31) == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+// ---------------------------------------------------------------------------
+// x sweep: one block per (row, tile of XT cells); 256 threads = 256 interfaces.
+// ---------------------------------------------------------------------------
+constexpr int kXThreads = 256;
+constexpr int kXTile = kXThreads - 5;      // output cells per block
+constexpr int kXCells = kXThreads + 5;     // staged cells per block
+
+template <typename T, int NV>
+constexpr size_t sweep_x_smem() { return sizeof(T) * NV * (kXCells + kXThreads); }
+
+template <typename T, int NV, int MODE>
+__global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
+  T* sf = su + NV * kXCells;                // [NV][kXThreads]
+  T dt = T(0);
+  if (A.dt) {
+    double d = *A.dt;
+    if (d == 0.0) return;  // the run has reached t_end: the step changes nothing
+    dt = T(d);
+  }
+  const int64_t row = blockIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * kXTile;
+  const int ntile = (int)min((int64_t)kXTile, A.nx - c0);
+  const T* base = A.u + row * A.pitch;
+  for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
+    const int v = idx / kXCells, s = idx - v * kXCells;
+    if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  bool fb = false;
+  if (t < ntile + 5) {
+    T S[6][NV];
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) S[m][k] = su[k * kXCells + t + m];
+    T F[NV];
+    fb = interface_flux<T, NV>(S, A.s, 0, F);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sf[k * kXThreads + t] = F[k];
+    // each interface of the line is counted by exactly one tile
+    const bool owned = (c0 + kXTile >= A.nx) ? true : (t < kXTile);
+    fb = fb && owned;
+  }
+  count_fallbacks(fb, A.fallbacks);
+  __syncthreads();
+  if (t < ntile) {
+    const int64_t off = row * A.pitch + c0 + t;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const T* f = sf + k * kXThreads + t;
+      T L = flux_difference<T>(f[0], f[1], f[2], f[3], f[4], f[5], A.inv_h);
+      if (MODE == kWriteL) {
+        A.out[k * A.fstride + off] = L;
+      } else {
+        T cur = su[k * kXCells + t + 5];
+        T v = A.b * (cur + dt * L);
+        if (A.a != T(0)) v = A.a * A.un[k * A.fstride + off] + v;
+        A.out[k * A.fstride + off] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y sweep: one block per (32 columns, YT rows); 32 x 8 threads, each thread
+// computes 8 interfaces of its column.  L = L_x (from R) + L_y.
+// ---------------------------------------------------------------------------
+constexpr int kYCols = 32;
+constexpr int kYRowsT = 8;                 // thread rows
+constexpr int kYPer = 8;                   // interfaces per thread
+constexpr int kYIfc = kYRowsT * kYPer;     // 64 interfaces per column
+constexpr int kYTile = kYIfc - 5;          // 59 output rows per block
+constexpr int kYCells = kYIfc + 5;         // 69 staged rows
+
+template <typename T, int NV>
+constexpr size_t sweep_y_smem() { return sizeof(T) * NV * (kYCells + kYIfc) * kYCols; }
+
+template <typename T, int NV, int MODE>
+__global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kYCells][kYCols]
+  T* sf = su + NV * kYCells * kYCols;       // [NV][kYIfc][kYCols]
+  T dt = T(0);
+  if (A.dt) {
+    double d = *A.dt;
+    if (d == 0.0) return;
+    dt = T(d);
+  }
+  const int64_t c0 = (int64_t)blockIdx.x * kYCols;
+  const int64_t r0 = (int64_t)blockIdx.y * kYTile;
+  const int ntile = (int)min((int64_t)kYTile, A.ny - r0);
+  const int ncol = (int)min((int64_t)kYCols, A.nx - c0);
+  const int tid = threadIdx.y * kYCols + threadIdx.x;
+  for (int idx = tid; idx < NV * kYCells * kYCols; idx += kYCols * kYRowsT) {
+    const int x = idx % kYCols;
+    const int rest = idx / kYCols;
+    const int s = rest % kYCells, v = rest / kYCells;
+    if (x < ncol && s < ntile + 10)
+      su[idx] = A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x;
+  // the sweep's normal ordering swaps the two momentum components
+  constexpr int p1 = (NV == 4) ? 2 : 1;
+  constexpr int p2 = (NV == 4) ? 1 : 2;
+  for (int q = 0; q < kYPer; ++q) {
+    const int t = threadIdx.y + kYRowsT * q;
+    bool fb = false;
+    if (tx < ncol && t < ntile + 5) {
+      T S[6][NV];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          const int src = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
+          S[m][k] = su[(src * kYCells + t + m) * kYCols + tx];
+        }
+      }
+      T F[NV];
+      fb = interface_flux<T, NV>(S, A.s, 1, F);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int dst = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
+        sf[(dst * kYIfc + t) * kYCols + tx] = F[k];
+      }
+      const bool owned = (r0 + kYTile >= A.ny) ? true : (t < kYTile);
+      fb = fb && owned;
+    }
+    count_fallbacks(fb, A.fallbacks);
+  }
+  __syncthreads();
+  if (tx < ncol) {
+    for (int q = 0; q < kYPer; ++q) {
+      const int t = threadIdx.y + kYRowsT * q;
+      if (t >= ntile) break;
+      const int64_t off = (r0 + t) * A.pitch + c0 + tx;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const T* f = sf + (k * kYIfc + t) * kYCols + tx;
+        T Ly = flux_difference<T>(f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
+                                  f[5 * kYCols], A.inv_h);
+        T L = A.R[k * A.fstride + off] + Ly;
+        if (MODE == kWriteL) {
+          A.out[k * A.fstride + off] = L;
+        } else {
+          T cur = su[(k * kYCells + t + 5) * kYCols + tx];
+          T v = A.b * (cur + dt * L);
+          if (A.a != T(0)) v = A.a * A.un[k * A.fstride + off] + v;
+          A.out[k * A.fstride + off] = v;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------------------
+// CFL step: max over cells of |u_d| + c per direction, then
+// dt = cfl / sum_d(max_d / h_d), clipped at t_end; the device time advances.
+// The last block to finish (ticket counter) combines the per-block partials.
+// ---------------------------------------------------------------------------
+struct DtArgs {
+  const void* u;
+  int64_t nx, ny, pitch, fstride;
+  int nvar, ndim, system, use_cfl;
+  double gamma, cfl, hx, hy, fixed_dt, t_end;
+  double adv_wave[2];    // |a_d| for advection
+  double* partials;      // 2 * gridDim.x
+  unsigned int* counter;
+  double* dt_out;
+  double* t;
+  long long* steps;
+  int* err;              // bit 0: non-physical state
+};
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
+  __shared__ double smx[kRedThreads / 32], smy[kRedThreads / 32];
+  __shared__ int s_last, s_bad;
+  const T* u = static_cast<const T*>(A.u);
+  double mx = 0.0, my = 0.0;
+  int bad = 0;
+  if (NV > 1) {
+    const int64_t ncell = A.nx * A.ny;
+    for (int64_t c = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * kRedThreads) {
+      const int64_t j = c / A.nx, i = c - j * A.nx;
+      const int64_t off = j * A.pitch + i;
+      // wave speeds in the state's own precision; the maxima are kept in FP64
+      const T rho = u[off];
+      const T mu = u[A.fstride + off];
+      const T mv = (NV == 4) ? u[2 * A.fstride + off] : T(0);
+      const T E = u[(NV - 1) * A.fstride + off];
+      const T inv = T(1) / rho;
+      const T ux = mu * inv, vy = mv * inv;
+      const T p = T(A.gamma - 1.0) * (E - T(0.5) * rho * (ux * ux + vy * vy));
+      if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
+      const T cs = Num<T>::sqrt_(T(A.gamma) * p * inv);
+      mx = fmax(mx, (double)(Num<T>::abs_(ux) + cs));
+      my = fmax(my, (double)(Num<T>::abs_(vy) + cs));
+    }
+  }
+  mx = warp_max(mx);
+  my = warp_max(my);
+  bad = __any_sync(0xffffffffu, bad);
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    smx[threadIdx.x >> 5] = mx;
+    smy[threadIdx.x >> 5] = my;
+    if (bad) atomicOr(&s_bad, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bx = 0.0, by = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) { bx = fmax(bx, smx[w]); by = fmax(by, smy[w]); }
+    A.partials[2 * blockIdx.x] = bx;
+    A.partials[2 * blockIdx.x + 1] = by;
+    if (s_bad) atomicOr(A.err, 1);
+    __threadfence();
+    unsigned int ticket = atomicAdd(A.counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double gx = 0.0, gy = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    gx = fmax(gx, __ldcg(&A.partials[2 * b]));
+    gy = fmax(gy, __ldcg(&A.partials[2 * b + 1]));
+  }
+  *A.counter = 0u;  // ready for the next launch
+  if (A.t == nullptr) {  // max-wave query: report the maxima, leave the time alone
+    A.dt_out[0] = gx;
+    A.dt_out[1] = gy;
+    return;
+  }
+  double d;
+  if (!A.use_cfl) {
+    d = A.fixed_dt;
+  } else {
+    if (NV == 1) { gx = A.adv_wave[0]; gy = A.adv_wave[1]; }
+    double s = gx / A.hx;
+    if (A.ndim == 2) s += gy / A.hy;
+    d = A.cfl / s;
+  }
+  if (__ldcg(A.err) & 1) d = 0.0;  // a non-physical state freezes the run (reported at sync)
+  double t = *A.t;
+  if (A.t_end > 0.0) {
+    double rem = A.t_end - t;
+    if (d > rem) d = rem;
+    if (!(d > 0.0)) d = 0.0;
+  }
+  *A.dt_out = d;
+  if (d > 0.0) {
+    *A.t = (A.t_end > 0.0 && d == A.t_end - t) ? A.t_end : t + d;
+    *A.steps += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions per variable plane: SUM, L1 (mean |a - b|), LINF (max |a - b|).
+// blockIdx.y = variable.  Partials [nvar][gridDim.x]; the last block per variable
+// writes out[v].
+// ---------------------------------------------------------------------------
+struct ReduceArgs {
+  const void* a;
+  const void* b;   // may be null
+  int64_t nx, ny, pitch, fstride;
+  int what;        // 0 sum, 1 l1, 2 linf
+  double* partials;
+  unsigned int* counters;  // one per variable
+  double* out;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs A) {
+  __shared__ double sacc[kRedThreads / 32];
+  __shared__ int s_last;
+  const T* a = static_cast<const T*>(A.a) + blockIdx.y * A.fstride;
+  const T* b = A.b ? static_cast<const T*>(A.b) + blockIdx.y * A.fstride : nullptr;
+  const int64_t ncell = A.nx * A.ny;
+  double acc = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * kRedThreads) {
+    const int64_t j = c / A.nx, i = c - j * A.nx;
+    double x = (double)a[j * A.pitch + i];
+    if (b) x -= (double)b[j * A.pitch + i];
+    if (A.what == 0) acc += x;
+    else if (A.what == 1) acc += fabs(x);
+    else acc = fmax(acc, fabs(x));
+  }
+  acc = (A.what == 2) ? warp_max(acc) : warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sacc[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) r = (A.what == 2) ? fmax(r, sacc[w]) : r + sacc[w];
+    A.partials[blockIdx.y * gridDim.x + blockIdx.x] = r;
+    __threadfence();
+    unsigned int ticket = atomicAdd(&A.counters[blockIdx.y], 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double r = 0.0;
+  for (int k = 0; k < (int)gridDim.x; ++k) {
+    double p = __ldcg(&A.partials[blockIdx.y * gridDim.x + k]);
+    r = (A.what == 2) ? fmax(r, p) : r + p;
+  }
+  A.counters[blockIdx.y] = 0u;
+  A.out[blockIdx.y] = (A.what == 1) ? r / (double)ncell : r;
+}
+
+}  // namespace wcns

@@ -1,0 +1,90 @@
+"""The C ABI library builds, loads without a GPU, exports every declared symbol, and
+rejects invalid descriptors before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_09760_gb300 import build as wbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    wbuild.build()
+    from paper_2306_09760_gb300 import wcns
+    return wcns
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(wcns_[a-z0-9_]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("wcns_init", "wcns_rhs", "wcns_step", "wcns_adjoint_step", "wcns_batch_init",
+                     "wcns_batch_step", "wcns_reduce", "wcns_sync_status", "wcns_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = lib.load()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_defaults(lib):
+    assert lib.wcns_status_string(0) == "ok"
+    assert "argument" in lib.wcns_status_string(1)
+    p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
+    assert p.weights == lib.WEIGHTS["FE"] and p.flux == lib.FLUXES["HLLC"]
+    assert p.xi == 1e6 and p.kappa == 0.5 and p.eps == 1e-40
+    p32 = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F32)
+    assert p32.eps == 1e-30
+    with pytest.raises(lib.WcnsError):
+        lib.wcns_default_params(7, 0)
+
+
+def _grid(lib, **kw):
+    g = lib.wcns_grid()
+    g.ndim, g.nvar, g.dtype, g.nx, g.ny, g.pitch = 1, 3, 0, 100, 1, 128
+    g.lo[0], g.hi[0] = 0.0, 1.0
+    g.bc[0] = 1
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+@pytest.mark.parametrize("bad", [dict(pitch=100), dict(pitch=64), dict(nx=0), dict(ny=2), dict(ndim=3),
+                                 dict(nvar=2), dict(dtype=5), dict(reserved=1)])
+def test_init_rejects_bad_grid_without_gpu(lib, bad):
+    p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
+    with pytest.raises(lib.WcnsError) as e:
+        lib.wcns_init(_grid(lib, **bad), p)
+    assert e.value.status == lib.WCNS_ERR_ARG
+
+
+def test_init_rejects_bad_params_without_gpu(lib):
+    g = _grid(lib)
+    for field, val, code in (("z_p", 3, 1), ("weights", 9, 1), ("eps", 0.0, 1), ("system", 0, 5)):
+        p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
+        setattr(p, field, val)
+        with pytest.raises(lib.WcnsError) as e:
+            lib.wcns_init(g, p)
+        assert e.value.status == code, field
+    # single precision JS weights need eps^2 to stay a normal float
+    g32 = _grid(lib, dtype=1)
+    p = lib.make_params(lib.WCNS_EULER, lib.WCNS_F32, weights="JS")
+    with pytest.raises(lib.WcnsError):
+        lib.wcns_init(g32, p)

@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64: relative max error max|gpu - oracle| / max|oracle| <= 1e-11 per run.
+FP32: mean absolute error per component <= 1e-5 (smooth) or 1e-3 (shocked) on states;
+      relative L1 <= 1e-4 on single RHS evaluations.
+Sizes span several tiles with ragged tails (x tiles of 251 cells, y tiles of 59 rows).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_09760_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2306_09760_gb300 import build as wbuild
+    wbuild.build()
+    from paper_2306_09760_gb300 import wcns
+    wcns.load()
+    return wcns
+
+
+@pytest.fixture(scope="module")
+def stream(W):
+    import torch
+    return torch.cuda.Stream()
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def self_sensitivity(P, run, seed=0):
+    """Relative max change of the oracle's own result when every input value is moved by
+    one ulp: the size of round-off amplification that any other rounding order (FMA
+    contraction, factored eigenvector products, CUDA's tanh) must be allowed."""
+    rng = np.random.default_rng(seed)
+    u1 = P.u0 * (1.0 + rng.choice([-1.0, 1.0], size=P.u0.shape) * 2.0 ** -52)
+    a = run(P.u0)
+    b = run(u1)
+    return rel_max(b, a)
+
+
+def l1(a, b):
+    return np.mean(np.abs(a - b), axis=tuple(range(1, a.ndim)))
+
+
+def gpu_rhs(W, stream, P, dtype="f64", **params):
+    import torch
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        L = S.numpy(S.rhs())
+        st, nonph = S.status()
+        S.close()
+    assert st == W.WCNS_OK, W.wcns_status_string(st)
+    return L, nonph
+
+
+def gpu_steps(W, stream, P, dtype="f64", dt=0.0, nsteps=1, t_end=0.0, **params):
+    import torch
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        S.step(dt, nsteps, t_end)
+        u = S.numpy()
+        t, taken = S.time()
+        st, nonph = S.status()
+        S.close()
+    assert st == W.WCNS_OK, W.wcns_status_string(st)
+    return u, t, taken, nonph
+
+
+def _adv(n, xi=1e6):
+    return inputs.advection_sine(n)
+
+
+RHS_CASES = [
+    ("advection_sine_200", lambda: inputs.advection_sine(200), {}),
+    ("advection_sine_200_xi100", lambda: inputs.advection_sine(200), dict(xi=100.0)),
+    ("advection_square_600_left", lambda: _square_wave(600, -1.0), {}),
+    ("sod_4096", lambda: inputs.sod(4096), {}),
+    ("shu_osher_4096", lambda: inputs.shu_osher(4096), {}),
+    ("lax_777", lambda: inputs.lax(777), dict(flux="ROE")),
+    ("riemann2d_300x130", lambda: inputs.riemann2d(300, seed=0, ny=130), {}),
+    ("riemann2d_eq38_257x131", lambda: inputs.riemann2d(257, seed="eq38", ny=131), {}),
+    ("smooth2d_periodic_300x130", lambda: inputs.random_smooth_euler_2d(300, 130, seed=3), {}),
+    ("vortex_64_llf_frozen", lambda: inputs.vortex(64, seed=1), dict(flux="LLF_FROZEN", alpha=(3.0, 3.0), xi=100.0)),
+]
+
+
+def _square_wave(n, speed):
+    x = -1.0 + np.arange(n) * (2.0 / n)
+    u0 = np.where(np.abs(x) < 0.4, 1.0, 0.0) + 0.2 * np.sin(3 * np.pi * x)
+    return inputs.Problem("square", 1, 1, n, 1, (-1.0, 0.0), (1.0, 1.0), (0, 0), u0[None, None, :].copy(), 0,
+                          adv_speed=(speed, 0.0))
+
+
+@pytest.mark.parametrize("name,make,params", RHS_CASES, ids=[c[0] for c in RHS_CASES])
+def test_rhs_parity_f64(W, stream, name, make, params):
+    P = make()
+    L, nonph = gpu_rhs(W, stream, P, "f64", **params)
+    Lr, nonph_r = oracle.rhs(P, **params)
+    assert rel_max(L, Lr) < TOL64, rel_max(L, Lr)
+    assert nonph == nonph_r
+
+
+@pytest.mark.parametrize("name,make,params", RHS_CASES, ids=[c[0] for c in RHS_CASES])
+def test_rhs_parity_f32(W, stream, name, make, params):
+    P = make()
+    L, _ = gpu_rhs(W, stream, P, "f32", **params)
+    Lr, _ = oracle.rhs(P, **params)
+    rel_l1 = np.abs(L - Lr).mean() / np.abs(Lr).mean()
+    assert rel_l1 < 1e-4, rel_l1
+
+
+@pytest.mark.parametrize("weights", ["JS", "Z", "FE", "PFE", "M"])
+@pytest.mark.parametrize("flux", ["LLF", "ROE", "HLLC"])
+@pytest.mark.parametrize("characteristic", [True, False])
+def test_option_matrix_rhs_parity(W, stream, weights, flux, characteristic):
+    P = inputs.random_piecewise_euler_1d(700, seed=5)
+    P2 = inputs.riemann2d(70, seed=2, ny=66)
+    params = dict(weights=weights, flux=flux, characteristic=characteristic)
+    for Q in (P, P2):
+        L, _ = gpu_rhs(W, stream, Q, "f64", **params)
+        Lr, _ = oracle.rhs(Q, **params)
+        assert rel_max(L, Lr) < TOL64, (Q.name, rel_max(L, Lr))
+
+
+def test_zp2_and_pfe(W, stream):
+    """Z exponent 2 and the PFE switch.  (Without renormalisation the sum of the mapped
+    weights on constant data depends on which plateau round-off noise selects, so that
+    reading has no well-defined parity and is not compared.)"""
+    P = inputs.shu_osher(1000)
+    for params in (dict(zp=2), dict(weights="PFE", cv=1e-2), dict(weights="PFE", cv=1e-3, xi=100.0)):
+        L, _ = gpu_rhs(W, stream, P, "f64", **params)
+        Lr, _ = oracle.rhs(P, **params)
+        assert rel_max(L, Lr) < TOL64, (params, rel_max(L, Lr))
+
+
+def test_advection_c1_full_run(W, stream):
+    """u_t + u_x = 0, periodic [-1, 1], N = 200, CFL 0.5, 400 TVD-RK3 steps to t = 2."""
+    P = inputs.advection_sine(200)
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=500, t_end=2.0)
+    ur, tr, takenr, _ = oracle.run_to(P, 2.0)
+    # 400 steps of 0.005 accumulate to just below 2; a final clipped step lands on t = 2
+    assert taken == takenr and 400 <= taken <= 401 and t == tr == 2.0
+    assert rel_max(u, ur) < TOL64, rel_max(u, ur)
+    # the exact solution after one period is the initial data
+    assert np.max(np.abs(ur - P.u0)) < 1e-4
+
+
+def test_sod_full_run_f64_f32(W, stream):
+    """Sod to t = 0.2 (N = 1024, ~900 steps).  Across a long shocked run the nonlinear
+    weights amplify round-off: the oracle itself moves by ~1e-7 when its input moves by one
+    ulp.  The GPU must agree to 1e-11 or to within 10x that intrinsic sensitivity."""
+    P = inputs.sod(1024)
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=2000, t_end=0.2)
+    ur, tr, takenr, _ = oracle.run_to(P, 0.2)
+    assert t == tr == 0.2 and taken == takenr
+    sens = self_sensitivity(P, lambda u0: oracle.run_to(P, 0.2, u=u0)[0])
+    err = rel_max(u, ur)
+    assert err < max(TOL64, 10 * sens), (err, sens)
+    u32, t32, _, _ = gpu_steps(W, stream, P, "f32", nsteps=2000, t_end=0.2)
+    assert abs(t32 - 0.2) < 1e-12
+    assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.sod(4096), lambda: inputs.shu_osher(4096)], ids=["sod", "shu_osher"])
+def test_1d_4096_steps(W, stream, make):
+    P = make()
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=150)
+    ur, tr, takenr, _ = oracle.step(P, nsteps=150)
+    assert taken == takenr == 150 and abs(t - tr) <= 1e-14 * tr
+    sens = self_sensitivity(P, lambda u0: oracle.step(P, u0, nsteps=150)[0])
+    err = rel_max(u, ur)
+    assert err < max(TOL64, 10 * sens), (err, sens)
+    u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=150)
+    assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
+
+
+def test_2d_steps(W, stream):
+    P = inputs.riemann2d(300, seed=0, ny=130)
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=20)
+    ur, tr, takenr, _ = oracle.step(P, nsteps=20)
+    assert rel_max(u, ur) < TOL64, rel_max(u, ur)
+    u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=20)
+    assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
+
+
+def test_2d_smooth_f32_l1(W, stream):
+    P = inputs.random_smooth_euler_2d(200, 120, seed=4)
+    ur, _, _, _ = oracle.step(P, nsteps=20)
+    u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=20)
+    assert np.all(l1(u32, ur) < 1e-5), l1(u32, ur)
+
+
+def test_reductions(W, stream):
+    import torch
+    P = inputs.riemann2d(300, seed=1, ny=130)
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f64", stream=stream)
+        other = S.alloc()
+        S.set_state(P.u0 * 1.5, other)
+        s = S.reduce(W.WCNS_REDUCE_SUM)
+        l1v = S.reduce(W.WCNS_REDUCE_L1, S.u, other)
+        linf = S.reduce(W.WCNS_REDUCE_LINF, S.u, other)
+        mw = S.reduce(W.WCNS_REDUCE_MAXWAVE)
+        S.close()
+    u = P.u0
+    np.testing.assert_allclose(s, u.sum(axis=(1, 2)), rtol=1e-13)
+    np.testing.assert_allclose(l1v, np.abs(0.5 * u).mean(axis=(1, 2)), rtol=1e-13)
+    np.testing.assert_allclose(linf, np.abs(0.5 * u).max(axis=(1, 2)), rtol=1e-15)
+    np.testing.assert_allclose(mw, oracle.max_wave(P), rtol=1e-14)
+
+
+def test_step_host_equals_step(W, stream):
+    import torch
+    P = inputs.riemann2d(100, seed=3, ny=70)
+    u_dev, _, _, _ = gpu_steps(W, stream, P, "f64", nsteps=3)
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f64", stream=stream)
+        host = torch.zeros((4, 70, S.grid.pitch), dtype=torch.float64).pin_memory()
+        host[:, :, :100] = torch.from_numpy(P.u0)
+        W.wcns_step_host(S.ctx, host, 0.0, 3, 0.0)
+        S.close()
+    np.testing.assert_array_equal(host[:, :, :100].numpy(), u_dev)
+
+
+def test_periodic_conservation_gpu(W, stream):
+    import torch
+    P = inputs.vortex(128, seed=2)
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f64", stream=stream)
+        s0 = S.reduce(W.WCNS_REDUCE_SUM)
+        S.step(0.0, 10)
+        s1 = S.reduce(W.WCNS_REDUCE_SUM)
+        S.close()
+    scale = np.abs(P.u0).sum(axis=(1, 2))
+    assert np.all(np.abs(s1 - s0) < 1e-13 * scale), (s1 - s0) / scale
+
+
+def test_nonphysical_input_is_reported(W, stream):
+    """A negative density in the input is caught by the step-size reduction and returned
+    as a sticky WCNS_ERR_NONPHYSICAL; the run freezes (dt = 0) instead of producing NaN."""
+    import torch
+    P = inputs.sod(300)
+    P.u0[0, 0, 100] = -1.0
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f64", stream=stream)
+        S.step(0.0, 3)
+        st, _ = S.status()
+        t, taken = S.time()
+        st2, _ = S.status()  # sticky status is cleared by the read
+        S.close()
+    assert st == W.WCNS_ERR_NONPHYSICAL and taken == 0 and t == 0.0
+    assert st2 == W.WCNS_OK
+
+
+def test_fixed_dt_and_graph_replay_match_direct(W, stream):
+    """Graph replay (stream, nsteps >= 2) and direct launches (one step at a time) agree."""
+    import torch
+    P = inputs.shu_osher(1500)
+    with torch.cuda.stream(stream):
+        A = W.Solver(P, "f64", stream=stream)
+        A.step(1e-4, 6)
+        B = W.Solver(P, "f64", stream=stream)
+        for _ in range(6):
+            B.step(1e-4, 1)
+        ua, ub = A.numpy(), B.numpy()
+        A.close(); B.close()
+    np.testing.assert_array_equal(ua, ub)
+    ur, _, _, _ = oracle.step(P, dt=1e-4, nsteps=6)
+    assert rel_max(ua, ur) < TOL64
