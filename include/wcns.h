@@ -145,11 +145,18 @@ wcns_status wcns_get_time(wcns_ctx* ctx, double* t, int64_t* steps_taken);
  * Accumulation is FP64 for both element types. */
 wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t what, double* out);
 
-/* Adjoint of one TVD-RK3 step of fixed size dt: given u_n and the cotangent lam_np1
- * of u_{n+1} = S(u_n), writes lam_n = (dS/du_n)^T lam_np1.  The stage states are
- * recomputed from u_n.  Supported: WCNS_EULER, ndim 2, WCNS_FLUX_LLF_FROZEN, weights
- * JS / Z / FE, characteristic 0 or 1; otherwise WCNS_ERR_UNSUPPORTED.  lam_np1 and
- * lam_n may be the same buffer.  Asynchronous. */
+/* Adjoint of one TVD-RK3 step of fixed size dt > 0 (the benchmark spec's hand-written
+ * adjoint of steps (a)-(e)): given the checkpoint u_n and the cotangent lam_np1 of
+ * u_{n+1} = S(u_n), writes lam_n = (dS/du_n)^T lam_np1.  The stage states u1, u2 are
+ * recomputed from u_n (they overwrite the context's stage scratch); the reverse
+ * sweeps differentiate the interface flux exactly, including the FE map (Eq. 20),
+ * the Z/JS weights (Eq. 11, 14-15), the characteristic projection and the Roe
+ * average, and scatter into cells by gathering (no atomics).
+ * Supported: WCNS_EULER (ndim 1 or 2), WCNS_FLUX_LLF_FROZEN (a smooth flux), weights
+ * JS / Z / FE / PFE, characteristic 0 or 1; otherwise WCNS_ERR_UNSUPPORTED.
+ * lam_np1 and lam_n may be the same buffer; u_n must not alias either.  The first
+ * call allocates two cotangent buffers of the context (nvar*ny*pitch each).
+ * Asynchronous. */
 wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const void* lam_np1,
                               void* lam_n);
 
@@ -168,7 +175,7 @@ wcns_status wcns_profile_enable(wcns_ctx* ctx, int32_t on);
 
 /* Synchronises the stream and returns, per kernel kind, its name (48-byte slots in
  * `names`), launches and total milliseconds since the last read, then resets them.
- * max_entries must be >= 7 (the number of kinds); *n_entries receives that number. */
+ * max_entries must be >= 9 (the number of kinds); *n_entries receives that number. */
 wcns_status wcns_profile_read(wcns_ctx* ctx, int32_t max_entries, char* names, int64_t* launches,
                               double* ms, int32_t* n_entries);
 

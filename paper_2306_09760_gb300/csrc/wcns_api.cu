@@ -23,6 +23,8 @@ struct wcns_ctx {
   void* u2;
   void* R;               // L_x planes (2D)
   void* host_state;      // device copy used by wcns_step_host (lazy)
+  void* adj1;            // adjoint stage cotangents (lazy)
+  void* adj2;
   // small device scalars (one allocation)
   void* scal;
   double* d_dt;
@@ -46,9 +48,9 @@ struct wcns_ctx {
 
 namespace {
 enum ProfKind { kProfSweepXRhs = 0, kProfSweepYRhs, kProfSweepXStage1D, kProfSweepXLx, kProfSweepYStage, kProfDt,
-                kProfReduce, kProfCount };
+                kProfReduce, kProfAdjX, kProfAdjY, kProfCount };
 const char* const kProfNames[kProfCount] = {"sweep_x_rhs", "sweep_y_rhs", "sweep_x_stage_1d", "sweep_x_lx_2d",
-                                            "sweep_y_stage_2d", "dt_cfl", "reduce"};
+                                            "sweep_y_stage_2d", "dt_cfl", "reduce", "adjoint_x", "adjoint_y"};
 }  // namespace
 
 namespace {
@@ -197,6 +199,32 @@ cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool 
     return by_type(c->g.dtype, [&] { return launch_dt<double>(c->gi, d, c->stream); },
                    [&] { return launch_dt<float>(c->gi, d, c->stream); });
   });
+}
+
+// out = c1 X1 + c2 X2 + b (mu + dt J(u)^T mu), J = dL/du (both sweeps).
+template <typename T>
+cudaError_t adjoint_stage(wcns_ctx* c, const void* u, const void* mu, const void* X1, double c1, const void* X2,
+                          double c2, double b, double dt, void* out) {
+  AdjCall<T> a{};
+  a.u = static_cast<const T*>(u);
+  a.mu = static_cast<const T*>(mu);
+  a.X1 = static_cast<const T*>(X1);
+  a.X2 = static_cast<const T*>(X2);
+  a.c1 = c1; a.c2 = c2; a.b = b; a.dt = dt;
+  if (c->g.ndim == 1) {
+    a.out = static_cast<T*>(out);
+    a.combine = true;
+    return timed(c, kProfAdjX, [&] { return launch_adjoint_x<T>(c->gi, c->s, a, c->stream); });
+  }
+  AdjCall<T> x = a;
+  x.out = static_cast<T*>(c->R);
+  x.combine = false;
+  cudaError_t e = timed(c, kProfAdjX, [&] { return launch_adjoint_x<T>(c->gi, c->s, x, c->stream); });
+  if (e != cudaSuccess) return e;
+  a.R = static_cast<const T*>(c->R);
+  a.out = static_cast<T*>(out);
+  a.combine = true;
+  return timed(c, kProfAdjY, [&] { return launch_adjoint_y<T>(c->gi, c->s, a, c->stream); });
 }
 
 // One TVD-RK3 step on u in place (Shu-Osher form).
@@ -425,9 +453,33 @@ wcns_status wcns_reduce(wcns_ctx* c, const void* a, const void* b, int32_t what,
 }
 
 wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const void* lam_np1, void* lam_n) {
-  if (!c || !u_n || !lam_np1 || !lam_n) return WCNS_ERR_ARG;
-  (void)dt;
-  return WCNS_ERR_UNSUPPORTED;
+  if (!c || !u_n || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(lam_np1) || !aligned16(lam_n))
+    return WCNS_ERR_ARG;
+  if (!(dt > 0.0)) return WCNS_ERR_ARG;
+  const wcns_params& p = c->p;
+  if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M) return WCNS_ERR_UNSUPPORTED;
+  const size_t bytes = c->nelem * c->elem;
+  if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
+  if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
+  // stage states of the forward step, recomputed from the checkpoint u_n
+  WCNS_TRY(cudaMemcpyAsync(c->d_dt, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  WCNS_TRY(stage(c, u_n, nullptr, c->u1, 0.0, 1.0));
+  WCNS_TRY(stage(c, c->u1, u_n, c->u2, 0.75, 0.25));
+  // reverse of u' = 1/3 u + 2/3 (u2 + dt L(u2)), u2 = 3/4 u + 1/4 (u1 + dt L(u1)), u1 = u + dt L(u):
+  //   a2 = 2/3 (lam + dt J(u2)^T lam)
+  //   a1 = 1/4 (a2 + dt J(u1)^T a2)
+  //   lam_n = 1/3 lam + 3/4 a2 + (a1 + dt J(u)^T a1)
+  auto reverse_stage = [&](const void* u, const void* mu, const void* X1, double c1, const void* X2, double c2,
+                           double b, void* out) -> cudaError_t {
+    return by_type(
+        c->g.dtype,
+        [&] { return adjoint_stage<double>(c, u, mu, X1, c1, X2, c2, b, dt, out); },
+        [&] { return adjoint_stage<float>(c, u, mu, X1, c1, X2, c2, b, dt, out); });
+  };
+  WCNS_TRY(reverse_stage(c->u2, lam_np1, nullptr, 0.0, nullptr, 0.0, 2.0 / 3.0, c->adj1));
+  WCNS_TRY(reverse_stage(c->u1, c->adj1, nullptr, 0.0, nullptr, 0.0, 0.25, c->adj2));
+  WCNS_TRY(reverse_stage(u_n, c->adj2, lam_np1, 1.0 / 3.0, c->adj1, 0.75, 1.0, lam_n));
+  return WCNS_OK;
 }
 
 wcns_status wcns_sync_status(wcns_ctx* c, int64_t* nonphysical) {
@@ -484,6 +536,8 @@ void wcns_destroy(wcns_ctx* c) {
   if (c->u2) cudaFree(c->u2);
   if (c->R) cudaFree(c->R);
   if (c->host_state) cudaFree(c->host_state);
+  if (c->adj1) cudaFree(c->adj1);
+  if (c->adj2) cudaFree(c->adj2);
   if (c->scal) cudaFree(c->scal);
   delete c;
 }

@@ -108,7 +108,7 @@ cudaError_t build_items(wcns_batch* b, int nt) {
   return e;
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int FIX>
 cudaError_t stage_launch(wcns_batch* b, const void* u, const void* un, void* out, double a, double c, int ticket,
                          const double* dt, int bps) {
   BatchStageArgs<T> A{};
@@ -126,21 +126,32 @@ cudaError_t stage_launch(wcns_batch* b, const void* u, const void* un, void* out
   A.bc = b->bc;
   A.a = T(a);
   A.b = T(c);
-  A.s = b->s;
+  A.s = scheme_as<T>(b->s);
   A.fallbacks = b->d_fallbacks;
-  batch_stage_kernel<T, NT><<<b->num_sms * bps, NT, 0, b->stream>>>(A);
+  batch_stage_kernel<T, NT, FIX><<<b->num_sms * bps, NT, 0, b->stream>>>(A);
   return cudaGetLastError();
+}
+
+bool batch_fixed(const Scheme& s) {
+  return s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1;
+}
+
+template <typename T, int FIX>
+cudaError_t stage_fix(wcns_batch* b, int nt, const void* u, const void* un, void* out, double a, double c, int ticket,
+                      const double* dt, int bps) {
+  switch (nt) {
+    case 128: return stage_launch<T, 128, FIX>(b, u, un, out, a, c, ticket, dt, bps);
+    case 256: return stage_launch<T, 256, FIX>(b, u, un, out, a, c, ticket, dt, bps);
+    case 512: return stage_launch<T, 512, FIX>(b, u, un, out, a, c, ticket, dt, bps);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t stage_any(wcns_batch* b, int nt, const void* u, const void* un, void* out, double a, double c, int ticket,
                       const double* dt, int bps) {
-  switch (nt) {
-    case 128: return stage_launch<T, 128>(b, u, un, out, a, c, ticket, dt, bps);
-    case 256: return stage_launch<T, 256>(b, u, un, out, a, c, ticket, dt, bps);
-    case 512: return stage_launch<T, 512>(b, u, un, out, a, c, ticket, dt, bps);
-  }
-  return cudaErrorInvalidValue;
+  return batch_fixed(b->s) ? stage_fix<T, 1>(b, nt, u, un, out, a, c, ticket, dt, bps)
+                           : stage_fix<T, 0>(b, nt, u, un, out, a, c, ticket, dt, bps);
 }
 
 cudaError_t stage(wcns_batch* b, const void* u, const void* un, void* out, double a, double c, int ticket,
@@ -149,16 +160,22 @@ cudaError_t stage(wcns_batch* b, const void* u, const void* un, void* out, doubl
                               : stage_any<float>(b, nt, u, un, out, a, c, ticket, dt, bps);
 }
 
-template <typename T>
-int max_blocks_per_sm(int nt) {
+template <typename T, int FIX>
+int max_blocks_fix(int nt) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (nt) {
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 128>, 128, 0); break;
-    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 256>, 256, 0); break;
-    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 512>, 512, 0); break;
+    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 128, FIX>, 128, 0); break;
+    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 256, FIX>, 256, 0); break;
+    case 512: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_kernel<T, 512, FIX>, 512, 0); break;
   }
   return e == cudaSuccess ? n : 0;
+}
+
+int max_blocks_per_sm(const wcns_batch* b, int nt) {
+  const bool f = batch_fixed(b->s);
+  if (b->dtype == WCNS_F64) return f ? max_blocks_fix<double, 1>(nt) : max_blocks_fix<double, 0>(nt);
+  return f ? max_blocks_fix<float, 1>(nt) : max_blocks_fix<float, 0>(nt);
 }
 
 cudaError_t dt_launch(wcns_batch* b, const void* u, double t_end, double* dt_out, int advance) {
@@ -203,7 +220,7 @@ cudaError_t autotune(wcns_batch* b, const void* u) {
   const int nts[3] = {128, 256, 512};
   for (int nt : nts) {
     if ((e = build_items(b, nt)) != cudaSuccess) break;
-    int maxb = b->dtype == WCNS_F64 ? max_blocks_per_sm<double>(nt) : max_blocks_per_sm<float>(nt);
+    int maxb = max_blocks_per_sm(b, nt);
     for (int bps = 1; bps <= maxb; bps *= 2) {
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
@@ -340,7 +357,7 @@ wcns_status wcns_batch_init(const int64_t* offsets, const int64_t* n, int32_t np
   if (e == cudaSuccess) e = cudaMemset(b->d_fallbacks, 0, 64);
   if (e == cudaSuccess && tile != 0) {
     b->nt = tile + 5;
-    int maxb = dtype == WCNS_F64 ? max_blocks_per_sm<double>(b->nt) : max_blocks_per_sm<float>(b->nt);
+    int maxb = max_blocks_per_sm(b, b->nt);
     b->bps = maxb > 0 ? maxb : 1;
     b->configured = true;
     e = build_items(b, b->nt);

@@ -31,12 +31,12 @@ struct BatchStageArgs {
   int64_t total;
   int bc;
   T a, b;
-  Scheme s;
+  SchemeT<T> s;
   unsigned long long* fallbacks;
 };
 
 // Persistent stage kernel; NT threads = NT - 5 output cells per work item.
-template <typename T, int NT>
+template <typename T, int NT, int FIX>
 __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
   constexpr int NV = 3;
   constexpr int TILE = NT - 5;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
 #pragma unroll
           for (int k = 0; k < NV; ++k) S[m][k] = su[k][t + m];
         T F[NV];
-        fb = interface_flux<T, NV>(S, A.s, 0, F);
+        fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
 #pragma unroll
         for (int k = 0; k < NV; ++k) sf[k][t] = F[k];
         const bool last = (c0 + TILE >= n);

@@ -32,6 +32,42 @@ struct Scheme {
   double null0[3], null1[4], null2[3];
 };
 
+// The same parameters in the kernel's own precision (no conversions inside kernels).
+template <typename T>
+struct SchemeT {
+  int system, weights, flux, characteristic, zp, renorm;
+  T gamma, gm1, eps, xi, cv, harten;
+  T speed[2];
+  T null0[3], null1[4], null2[3];
+};
+
+template <typename T>
+inline SchemeT<T> scheme_as(const Scheme& s) {
+  SchemeT<T> r;
+  r.system = s.system; r.weights = s.weights; r.flux = s.flux;
+  r.characteristic = s.characteristic; r.zp = s.zp; r.renorm = s.renorm;
+  r.gamma = T(s.gamma); r.gm1 = T(s.gamma - 1.0); r.eps = T(s.eps); r.xi = T(s.xi);
+  r.cv = T(s.cv); r.harten = T(s.harten);
+  for (int d = 0; d < 2; ++d) r.speed[d] = T(s.speed[d]);
+  for (int j = 0; j < 3; ++j) { r.null0[j] = T(s.null0[j]); r.null2[j] = T(s.null2[j]); }
+  for (int j = 0; j < 4; ++j) r.null1[j] = T(s.null1[j]);
+  return r;
+}
+
+// Compile-time specialisation of the option switches.  FIX = 0: every option read
+// from the scheme at run time.  FIX = 1: FE weights (Z, p = 1, renormalised), HLLC,
+// characteristic projection -- the default configuration, compiled without the
+// other branches.
+template <int FIX> struct Fixed {
+  static constexpr bool on = false;
+  static constexpr int weights = 0, flux = 0, characteristic = 0, zp = 1, renorm = 1;
+};
+template <> struct Fixed<1> {
+  static constexpr bool on = true;
+  static constexpr int weights = 2, flux = 2, characteristic = 1, zp = 1, renorm = 1;
+};
+#define WCNS_OPT(FIX, s, field) (Fixed<FIX>::on ? Fixed<FIX>::field : (s).field)
+
 // ---------------------------------------------------------------------------
 // Small math helpers
 // ---------------------------------------------------------------------------
@@ -67,39 +103,105 @@ WCNS_HD T tanh_sat(T z) {
 // with omega_{i,0} = omega_{i,J} = w.  The map is a smoothed staircase whose
 // plateaus are the control values.
 // ---------------------------------------------------------------------------
+// Exact evaluation of map i at w (any tanh argument).
 template <typename T>
-WCNS_HD T fe_map0(T w, const Scheme& s) {
-  const T xi = T(s.xi);
-  T t1 = tanh_sat<T>(xi * (w - T(s.null0[0])));
-  T t2 = tanh_sat<T>(xi * (w - T(s.null0[1])));
-  T t3 = tanh_sat<T>(xi * (w - T(s.null0[2])));
-  T acc = ((T(1.0 / 16.0) - w) / T(2)) * t1;
-  acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * t2;
-  acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * t3;
-  return acc + w;
-}
-template <typename T>
-WCNS_HD T fe_map1(T w, const Scheme& s) {
-  const T xi = T(s.xi);
-  T t1 = tanh_sat<T>(xi * (w - T(s.null1[0])));
-  T t2 = tanh_sat<T>(xi * (w - T(s.null1[1])));
-  T t3 = tanh_sat<T>(xi * (w - T(s.null1[2])));
-  T t4 = tanh_sat<T>(xi * (w - T(s.null1[3])));
-  T acc = ((T(10.0 / 16.0) - w) / T(2)) * t1;
-  acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * t2;
-  acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * t3;
-  acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * t4;
-  return acc + w;
-}
-template <typename T>
-WCNS_HD T fe_map2(T w, const Scheme& s) {
-  const T xi = T(s.xi);
-  T t1 = tanh_sat<T>(xi * (w - T(s.null2[0])));
-  T t2 = tanh_sat<T>(xi * (w - T(s.null2[1])));
-  T t3 = tanh_sat<T>(xi * (w - T(s.null2[2])));
+WCNS_HD T fe_map_exact(int i, T w, const SchemeT<T>& s) {
+  const T xi = s.xi;
+  if (i == 0) {
+    T t1 = tanh_sat<T>(xi * (w - s.null0[0]));
+    T t2 = tanh_sat<T>(xi * (w - s.null0[1]));
+    T t3 = tanh_sat<T>(xi * (w - s.null0[2]));
+    T acc = ((T(1.0 / 16.0) - w) / T(2)) * t1;
+    acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * t2;
+    acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * t3;
+    return acc + w;
+  }
+  if (i == 1) {
+    T t1 = tanh_sat<T>(xi * (w - s.null1[0]));
+    T t2 = tanh_sat<T>(xi * (w - s.null1[1]));
+    T t3 = tanh_sat<T>(xi * (w - s.null1[2]));
+    T t4 = tanh_sat<T>(xi * (w - s.null1[3]));
+    T acc = ((T(10.0 / 16.0) - w) / T(2)) * t1;
+    acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * t2;
+    acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * t3;
+    acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * t4;
+    return acc + w;
+  }
+  T t1 = tanh_sat<T>(xi * (w - s.null2[0]));
+  T t2 = tanh_sat<T>(xi * (w - s.null2[1]));
+  T t3 = tanh_sat<T>(xi * (w - s.null2[2]));
   T acc = ((T(5.0 / 16.0) - w) / T(2)) * t1;
   acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * t2;
   acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * t3;
+  return acc + w;
+}
+
+// Out-of-line copy of the exact map: the tanh code exists once per kernel instead of
+// once per inlined call site.
+template <typename T>
+__host__ __device__ __noinline__ T fe_map_slow(int i, T w, const SchemeT<T>& s) {
+  return fe_map_exact<T>(i, w, s);
+}
+
+// Sign of z as the value tanh(z) rounds to once |z| >= kSat.
+template <typename T>
+WCNS_HD T sat_sign(T z) { return z > T(0) ? T(1) : T(-1); }
+
+// Saturation test of xi (w - n) for every null point n of one map.  In double
+// precision the test runs in single precision (fast pipe) with a margin that covers
+// the rounding of w, n and xi * (w - n) to float: |xi (w - n)| >= 20 holds whenever the
+// float estimate is >= 20 + 1e-4 + 1.2e-7 * xi * (|w| + |n|).  The signs are then exact.
+template <typename T, int K>
+WCNS_HD bool all_saturated(T w, const T (&n)[K], T xi) {
+  if constexpr (sizeof(T) == 8) {
+    const float wf = (float)w, xf = (float)xi;
+    bool sat = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float nf = (float)n[j];
+      const float z = xf * (wf - nf);
+      const float margin = 1.0e-4f + 1.2e-7f * xf * (fabsf(wf) + fabsf(nf));
+      sat = sat && (fabsf(z) >= 20.0f + margin);
+    }
+    return sat;
+  } else {
+    bool sat = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) sat = sat && (Num<T>::abs_(xi * (w - n[j])) >= Num<T>::kSat);
+    return sat;
+  }
+}
+
+// Sign of w - n once the test above passed (|w - n| is then far from zero).
+template <typename T>
+WCNS_HD T side_of(T w, T n) { return w > n ? T(1) : T(-1); }
+
+// Eq. 20 for weight i.  When every tanh argument is saturated (the usual case at
+// large xi) each term is exactly +-amplitude and the map is evaluated with signs;
+// otherwise the exact out-of-line path runs.  Both give the same value there.
+template <typename T>
+WCNS_HD T fe_map0(T w, const SchemeT<T>& s) {
+  if (!all_saturated<T, 3>(w, s.null0, s.xi)) return fe_map_slow<T>(0, w, s);
+  T acc = ((T(1.0 / 16.0) - w) / T(2)) * side_of(w, s.null0[0]);
+  acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * side_of(w, s.null0[1]);
+  acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * side_of(w, s.null0[2]);
+  return acc + w;
+}
+template <typename T>
+WCNS_HD T fe_map1(T w, const SchemeT<T>& s) {
+  if (!all_saturated<T, 4>(w, s.null1, s.xi)) return fe_map_slow<T>(1, w, s);
+  T acc = ((T(10.0 / 16.0) - w) / T(2)) * side_of(w, s.null1[0]);
+  acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * side_of(w, s.null1[1]);
+  acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * side_of(w, s.null1[2]);
+  acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * side_of(w, s.null1[3]);
+  return acc + w;
+}
+template <typename T>
+WCNS_HD T fe_map2(T w, const SchemeT<T>& s) {
+  if (!all_saturated<T, 3>(w, s.null2, s.xi)) return fe_map_slow<T>(2, w, s);
+  T acc = ((T(5.0 / 16.0) - w) / T(2)) * side_of(w, s.null2[0]);
+  acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * side_of(w, s.null2[1]);
+  acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * side_of(w, s.null2[2]);
   return acc + w;
 }
 
@@ -111,8 +213,11 @@ WCNS_HD T m_map(T w, T d) {
 
 // Midpoint value at x_{i+1/2} from five values v0..v4 = u_{i-2}..u_{i+2} (left state), or
 // the mirrored u_{i+3}..u_{i-1} (right state).  Returns the interpolated value.
-template <typename T>
-WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const Scheme& s) {
+template <typename T, int FIX>
+WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
+  const int weights = WCNS_OPT(FIX, s, weights);
+  const int zp = WCNS_OPT(FIX, s, zp);
+  const int renorm = WCNS_OPT(FIX, s, renorm);
   const T d0 = T(1.0 / 16.0), d1 = T(10.0 / 16.0), d2 = T(5.0 / 16.0);
   // Eq. 5
   T q0 = (T(3) * v0 - T(10) * v1 + T(15) * v2) / T(8);
@@ -125,42 +230,50 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const Scheme& s) {
   T is0 = f0 * f0 + s0 * s0;
   T is1 = f1 * f1 + s1 * s1;
   T is2 = f2 * f2 + s2 * s2;
-  const T eps = T(s.eps);
+  const T eps = s.eps;
   T w0, w1, w2;
-  if (s.weights == 0 || s.weights == 4) {
+  if (weights == 0 || weights == 4) {
     // Eq. 11
     T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
     T a0 = d0 / (b0 * b0), a1 = d1 / (b1 * b1), a2 = d2 / (b2 * b2);
-    T sa = a0 + a1 + a2;
-    w0 = a0 / sa; w1 = a1 / sa; w2 = a2 / sa;
-    if (s.weights == 4) {
+    const T isa = T(1) / (a0 + a1 + a2);
+    w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
+    if (weights == 4) {
       // Eq. 12-13
       T g0 = m_map<T>(w0, d0), g1 = m_map<T>(w1, d1), g2 = m_map<T>(w2, d2);
-      T sg = g0 + g1 + g2;
-      w0 = g0 / sg; w1 = g1 / sg; w2 = g2 / sg;
+      const T isg = T(1) / (g0 + g1 + g2);
+      w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;
     }
   } else {
     // Eq. 14-15
     T tau = Num<T>::abs_(is0 - is2);
-    T r0 = tau / (is0 + eps), r1 = tau / (is1 + eps), r2 = tau / (is2 + eps);
-    if (s.zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
+    T r0, r1, r2;
+    const T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
+    if constexpr (sizeof(T) == 8) {
+      // one division for the three ratios (the product of three IS + eps stays in range)
+      const T q = tau / (b0 * b1 * b2);
+      r0 = q * (b1 * b2); r1 = q * (b0 * b2); r2 = q * (b0 * b1);
+    } else {
+      r0 = tau / b0; r1 = tau / b1; r2 = tau / b2;
+    }
+    if (zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
     T a0 = d0 * (T(1) + r0), a1 = d1 * (T(1) + r1), a2 = d2 * (T(1) + r2);
-    T sa = a0 + a1 + a2;
-    w0 = a0 / sa; w1 = a1 / sa; w2 = a2 / sa;
-    if (s.weights >= 2) {
+    const T isa = T(1) / (a0 + a1 + a2);
+    w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
+    if (weights >= 2) {
       bool keep = false;
-      if (s.weights == 3) {
+      if (weights == 3) {
         // App. A: keep the Z weights inside the closed box |w_k - d_k| <= cv
-        const T cv = T(s.cv);
+        const T cv = s.cv;
         keep = (w0 >= d0 - cv) && (w0 <= d0 + cv) && (w1 >= d1 - cv) && (w1 <= d1 + cv) &&
                (w2 >= d2 - cv) && (w2 <= d2 + cv);
       }
       if (!keep) {
         // Eq. 20 on each weight, then renormalised
         T g0 = fe_map0<T>(w0, s), g1 = fe_map1<T>(w1, s), g2 = fe_map2<T>(w2, s);
-        if (s.renorm) {
-          T sg = g0 + g1 + g2;
-          w0 = g0 / sg; w1 = g1 / sg; w2 = g2 / sg;
+        if (renorm) {
+          const T isg = T(1) / (g0 + g1 + g2);
+          w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;
         } else {
           w0 = g0; w1 = g1; w2 = g2;
         }
@@ -276,18 +389,19 @@ WCNS_HD void char_unproject(const CharBasis<T, NV>& cb, const T (&W)[NV], T (&U)
 }
 
 // Approximate Riemann solvers (Eq. 6).
-template <typename T, int NV>
-WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const Scheme& s, int dir,
+template <typename T, int NV, int FIX>
+WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, int dir,
                                         T (&F)[NV]) {
-  const T g = T(s.gamma), gm1 = T(s.gamma - 1.0);
+  const int flux = WCNS_OPT(FIX, s, flux);
+  const T g = s.gamma, gm1 = s.gm1;
   EulerState<T, NV> a = euler_prim<T, NV>(UL, gm1), b = euler_prim<T, NV>(UR, gm1);
   T FL[NV], FR[NV];
   euler_flux<T, NV>(UL, a, FL);
   euler_flux<T, NV>(UR, b, FR);
-  if (s.flux == 0 || s.flux == 3) {
+  if (flux == 0 || flux == 3) {
     T alpha;
-    if (s.flux == 3) {
-      alpha = T(s.speed[dir]);
+    if (flux == 3) {
+      alpha = s.speed[dir];
     } else {
       T sl = Num<T>::abs_(a.un) + Num<T>::sqrt_(g * a.p / a.rho);
       T sr = Num<T>::abs_(b.un) + Num<T>::sqrt_(g * b.p / b.rho);
@@ -298,14 +412,14 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const Scheme& s, int 
     return;
   }
   RoeAvg<T, NV> r = roe_avg<T, NV>(a, b, gm1);
-  if (s.flux == 1) {
+  if (flux == 1) {
     // Roe: F = (FL + FR)/2 - 1/2 R |Lambda| L (UR - UL), Harten's fix on u -/+ c
     CharBasis<T, NV> cb = char_basis<T, NV>(r, gm1);
     T dU[NV], dW[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) dU[k] = UR[k] - UL[k];
     char_project<T, NV>(cb, dU, dW);
-    T delta = T(s.harten) * (Num<T>::abs_(r.u) + r.c);
+    T delta = s.harten * (Num<T>::abs_(r.u) + r.c);
     T l0 = Num<T>::abs_(r.u - r.c), lm = Num<T>::abs_(r.u), l3 = Num<T>::abs_(r.u + r.c);
     if (l0 < delta) l0 = ((r.u - r.c) * (r.u - r.c) + delta * delta) / (T(2) * delta);
     if (l3 < delta) l3 = ((r.u + r.c) * (r.u + r.c) + delta * delta) / (T(2) * delta);
@@ -367,19 +481,19 @@ WCNS_HD bool physical(const T (&U)[NV], T gm1) {
 // Midpoint flux at one interface from the six stencil states S[0..5] = U_{i-2..i+3}
 // (already in the sweep's normal ordering).  Returns true if the interpolated states
 // were non-physical and the interface fell back to (U_i, U_{i+1}).
-template <typename T, int NV>
-WCNS_HD bool interface_flux(const T (&S)[6][NV], const Scheme& s, int dir, T (&F)[NV]) {
+template <typename T, int NV, int FIX>
+WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV]) {
   if (NV == 1) {
-    const T a = T(s.speed[dir]);
+    const T a = s.speed[dir];
     T v;
-    if (a >= T(0)) v = weno_side<T>(S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
-    else v = weno_side<T>(S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
+    if (a >= T(0)) v = weno_side<T, FIX>(S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
+    else v = weno_side<T, FIX>(S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
     F[0] = a * v;
     return false;
   }
-  const T gm1 = T(s.gamma - 1.0);
+  const T gm1 = s.gm1;
   T UL[NV], UR[NV];
-  if (s.characteristic) {
+  if (WCNS_OPT(FIX, s, characteristic)) {
     T Ui[NV], Uj[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) { Ui[k] = S[2][k]; Uj[k] = S[3][k]; }
@@ -392,16 +506,16 @@ WCNS_HD bool interface_flux(const T (&S)[6][NV], const Scheme& s, int dir, T (&F
     T WL[NV], WR[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      WL[k] = weno_side<T>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
-      WR[k] = weno_side<T>(W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
+      WL[k] = weno_side<T, FIX>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
+      WR[k] = weno_side<T, FIX>(W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
     }
     char_unproject<T, NV>(cb, WL, UL);
     char_unproject<T, NV>(cb, WR, UR);
   } else {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      UL[k] = weno_side<T>(S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
-      UR[k] = weno_side<T>(S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
+      UL[k] = weno_side<T, FIX>(S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
+      UR[k] = weno_side<T, FIX>(S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
     }
   }
   bool fallback = false;
@@ -410,7 +524,7 @@ WCNS_HD bool interface_flux(const T (&S)[6][NV], const Scheme& s, int dir, T (&F
 #pragma unroll
     for (int k = 0; k < NV; ++k) { UL[k] = S[2][k]; UR[k] = S[3][k]; }
   }
-  riemann<T, NV>(UL, UR, s, dir, F);
+  riemann<T, NV, FIX>(UL, UR, s, dir, F);
   return fallback;
 }
 

@@ -40,6 +40,24 @@ cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T
 template <typename T>
 cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
 
+// Adjoint sweep: out = c1*X1 + c2*X2 + b*(mu + dt*(R + J^T mu)) (combine) or
+// out = J^T mu (x part of a 2D grid, combine == false).
+template <typename T>
+struct AdjCall {
+  const T* u;
+  const T* mu;
+  const T* R;
+  const T* X1;
+  const T* X2;
+  T* out;
+  double c1, c2, b, dt;
+  bool combine;
+};
+template <typename T>
+cudaError_t launch_adjoint_x(const GridInfo& g, const Scheme& s, const AdjCall<T>& c, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint_y(const GridInfo& g, const Scheme& s, const AdjCall<T>& c, cudaStream_t st);
+
 struct DtLaunch {
   const void* u;
   double cfl, fixed_dt, t_end;

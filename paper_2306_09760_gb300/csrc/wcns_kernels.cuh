@@ -30,7 +30,7 @@ struct SweepArgs {
   int64_t nx, ny, pitch, fstride;  // fstride = ny * pitch (elements per variable plane)
   int bc;              // boundary of this sweep's direction
   T inv_h;
-  Scheme s;
+  SchemeT<T> s;
   unsigned long long* fallbacks;   // interfaces that fell back to first order
 };
 
@@ -51,7 +51,7 @@ constexpr int kXCells = kXThreads + 5;     // staged cells per block
 template <typename T, int NV>
 constexpr size_t sweep_x_smem() { return sizeof(T) * NV * (kXCells + kXThreads); }
 
-template <typename T, int NV, int MODE>
+template <typename T, int NV, int MODE, int FIX>
 __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) S[m][k] = su[k * kXCells + t + m];
     T F[NV];
-    fb = interface_flux<T, NV>(S, A.s, 0, F);
+    fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
 #pragma unroll
     for (int k = 0; k < NV; ++k) sf[k * kXThreads + t] = F[k];
     // each interface of the line is counted by exactly one tile
@@ -121,7 +121,7 @@ constexpr int kYCells = kYIfc + 5;         // 69 staged rows
 template <typename T, int NV>
 constexpr size_t sweep_y_smem() { return sizeof(T) * NV * (kYCells + kYIfc) * kYCols; }
 
-template <typename T, int NV, int MODE>
+template <typename T, int NV, int MODE, int FIX>
 __global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kYCells][kYCols]
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> 
         }
       }
       T F[NV];
-      fb = interface_flux<T, NV>(S, A.s, 1, F);
+      fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const int dst = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
@@ -243,10 +243,16 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
   int bad = 0;
   if (NV > 1) {
     const int64_t ncell = A.nx * A.ny;
-    for (int64_t c = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; c < ncell;
-         c += (int64_t)gridDim.x * kRedThreads) {
-      const int64_t j = c / A.nx, i = c - j * A.nx;
+    // walk the flattened cell index with (row, column) kept incrementally
+    const int64_t stride = (int64_t)gridDim.x * kRedThreads;
+    const int64_t c0 = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+    const int64_t sj = stride / A.nx, si = stride - sj * A.nx;
+    int64_t j = c0 / A.nx, i = c0 - j * A.nx;
+    for (int64_t c = c0; c < ncell; c += stride) {
       const int64_t off = j * A.pitch + i;
+      i += si;
+      j += sj;
+      if (i >= A.nx) { i -= A.nx; ++j; }
       // wave speeds in the state's own precision; the maxima are kept in FP64
       const T rho = u[off];
       const T mu = u[A.fstride + off];
@@ -283,13 +289,25 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
     s_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
+  // the last block combines the per-block maxima with all of its threads
   __threadfence();
   double gx = 0.0, gy = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kRedThreads) {
     gx = fmax(gx, __ldcg(&A.partials[2 * b]));
     gy = fmax(gy, __ldcg(&A.partials[2 * b + 1]));
   }
+  gx = warp_max(gx);
+  gy = warp_max(gy);
+  if ((threadIdx.x & 31) == 0) {
+    smx[threadIdx.x >> 5] = gx;
+    smy[threadIdx.x >> 5] = gy;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  gx = 0.0;
+  gy = 0.0;
+  for (int w = 0; w < kRedThreads / 32; ++w) { gx = fmax(gx, smx[w]); gy = fmax(gy, smy[w]); }
   *A.counter = 0u;  // ready for the next launch
   if (A.t == nullptr) {  // max-wave query: report the maxima, leave the time alone
     A.dt_out[0] = gx;
@@ -342,11 +360,17 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs A) {
   const T* b = A.b ? static_cast<const T*>(A.b) + blockIdx.y * A.fstride : nullptr;
   const int64_t ncell = A.nx * A.ny;
   double acc = 0.0;
-  for (int64_t c = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; c < ncell;
-       c += (int64_t)gridDim.x * kRedThreads) {
-    const int64_t j = c / A.nx, i = c - j * A.nx;
-    double x = (double)a[j * A.pitch + i];
-    if (b) x -= (double)b[j * A.pitch + i];
+  const int64_t stride = (int64_t)gridDim.x * kRedThreads;
+  const int64_t c0 = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  const int64_t sj = stride / A.nx, si = stride - sj * A.nx;
+  int64_t j = c0 / A.nx, i = c0 - j * A.nx;
+  for (int64_t c = c0; c < ncell; c += stride) {
+    const int64_t off = j * A.pitch + i;
+    i += si;
+    j += sj;
+    if (i >= A.nx) { i -= A.nx; ++j; }
+    double x = (double)a[off];
+    if (b) x -= (double)b[off];
     if (A.what == 0) acc += x;
     else if (A.what == 1) acc += fabs(x);
     else acc = fmax(acc, fabs(x));
@@ -363,13 +387,20 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(ReduceArgs A) {
     s_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
   double r = 0.0;
-  for (int k = 0; k < (int)gridDim.x; ++k) {
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += kRedThreads) {
     double p = __ldcg(&A.partials[blockIdx.y * gridDim.x + k]);
     r = (A.what == 2) ? fmax(r, p) : r + p;
   }
+  r = (A.what == 2) ? warp_max(r) : warp_sum(r);
+  __syncthreads();  // sacc is reused
+  if ((threadIdx.x & 31) == 0) sacc[threadIdx.x >> 5] = r;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  r = 0.0;
+  for (int w = 0; w < kRedThreads / 32; ++w) r = (A.what == 2) ? fmax(r, sacc[w]) : r + sacc[w];
   A.counters[blockIdx.y] = 0u;
   A.out[blockIdx.y] = (A.what == 1) ? r / (double)ncell : r;
 }

@@ -3,23 +3,32 @@
 
 #include "wcns_internal.h"
 #include "wcns_kernels.cuh"
+#include "wcns_adjoint_kernels.cuh"
 
 namespace wcns {
 
+// FIX = 1 (compile-time default configuration) applies to the Euler systems only.
+template <int NV>
+static bool use_fixed(const Scheme& s) {
+  return NV > 1 && s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1;
+}
+
 template <typename T, int NV, int MODE>
-static cudaError_t run_sweep_x(const GridInfo& g, const SweepArgs<T>& A, cudaStream_t st) {
+static cudaError_t run_sweep_x(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
   const size_t smem = sweep_x_smem<T, NV>();
   dim3 grid((unsigned)((g.nx + kXTile - 1) / kXTile), (unsigned)g.ny);
-  sweep_x_kernel<T, NV, MODE><<<grid, kXThreads, smem, st>>>(A);
+  if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0)><<<grid, kXThreads, smem, st>>>(A);
+  else sweep_x_kernel<T, NV, MODE, 0><<<grid, kXThreads, smem, st>>>(A);
   return cudaGetLastError();
 }
 
 template <typename T, int NV, int MODE>
-static cudaError_t run_sweep_y(const GridInfo& g, const SweepArgs<T>& A, cudaStream_t st) {
+static cudaError_t run_sweep_y(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
   const size_t smem = sweep_y_smem<T, NV>();
   dim3 grid((unsigned)((g.nx + kYCols - 1) / kYCols), (unsigned)((g.ny + kYTile - 1) / kYTile));
   dim3 block(kYCols, kYRowsT);
-  sweep_y_kernel<T, NV, MODE><<<grid, block, smem, st>>>(A);
+  if (fixed) sweep_y_kernel<T, NV, MODE, (NV > 1 ? 1 : 0)><<<grid, block, smem, st>>>(A);
+  else sweep_y_kernel<T, NV, MODE, 0><<<grid, block, smem, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -29,43 +38,124 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   A.nx = g.nx; A.ny = g.ny; A.pitch = g.pitch; A.fstride = g.ny * g.pitch;
   A.bc = g.bc[dir];
   A.inv_h = T(1.0 / g.h[dir]);
-  A.s = s;
+  A.s = scheme_as<T>(s);
   A.fallbacks = c.fallbacks;
   A.u = c.u; A.un = c.un; A.R = c.R; A.out = c.out; A.dt = c.dt;
   A.a = T(c.a); A.b = T(c.b);
   return A;
 }
 
+template <typename T, int NV, int FIX>
+static cudaError_t configure_fix() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
+  if constexpr (NV == 3) {
+    return cudaSuccess;  // no y sweep in 1D Euler
+  } else {
+    if ((e = cudaFuncSetAttribute(sweep_y_kernel<T, NV, kWriteL, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_y_smem<T, NV>())) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_y_kernel<T, NV, kStage, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_y_smem<T, NV>());
+  }
+}
+
 template <typename T, int NV>
 static cudaError_t configure_nv() {
+  cudaError_t e = configure_fix<T, NV, 0>();
+  if constexpr (NV == 1) {
+    return e;
+  } else {
+    if (e != cudaSuccess) return e;
+    return configure_fix<T, NV, 1>();
+  }
+}
+
+template <typename T, int NV>
+static cudaError_t configure_adjoint() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_y_kernel<T, NV, kWriteL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_y_smem<T, NV>())) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_y_kernel<T, NV, kStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sweep_y_smem<T, NV>());
+  if ((e = cudaFuncSetAttribute(adjoint_x_kernel<T, NV, kAdjWrite>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj_x_smem<T, NV>())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(adjoint_x_kernel<T, NV, kAdjCombine>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj_x_smem<T, NV>())) != cudaSuccess) return e;
+  if constexpr (NV == 4) {
+    return cudaFuncSetAttribute(adjoint_y_kernel<T, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)adj_y_smem<T, NV>());
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t configure_kernels(int nvar) {
+  cudaError_t e;
   switch (nvar) {
     case 1: return configure_nv<T, 1>();
-    case 3: return configure_nv<T, 3>();
-    case 4: return configure_nv<T, 4>();
+    case 3:
+      if ((e = configure_nv<T, 3>()) != cudaSuccess) return e;
+      return configure_adjoint<T, 3>();
+    case 4:
+      if ((e = configure_nv<T, 4>()) != cudaSuccess) return e;
+      return configure_adjoint<T, 4>();
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static AdjArgs<T> make_adj_args(const GridInfo& g, const Scheme& s, int dir, const AdjCall<T>& c) {
+  AdjArgs<T> A{};
+  A.u = c.u; A.mu = c.mu; A.R = c.R; A.X1 = c.X1; A.X2 = c.X2; A.out = c.out;
+  A.c1 = T(c.c1); A.c2 = T(c.c2); A.b = T(c.b); A.dt = T(c.dt);
+  A.nx = g.nx; A.ny = g.ny; A.pitch = g.pitch; A.fstride = g.ny * g.pitch;
+  A.bc = g.bc[dir];
+  A.inv_h = T(1.0 / g.h[dir]);
+  A.s = scheme_as<T>(s);
+  return A;
+}
+
+template <typename T>
+cudaError_t launch_adjoint_x(const GridInfo& g, const Scheme& s, const AdjCall<T>& c, cudaStream_t st) {
+  AdjArgs<T> A = make_adj_args<T>(g, s, 0, c);
+  dim3 grid((unsigned)((g.nx + kXTile - 1) / kXTile), (unsigned)g.ny);
+  switch (g.nvar) {
+    case 3:
+      if (c.combine) adjoint_x_kernel<T, 3, kAdjCombine><<<grid, kXThreads, adj_x_smem<T, 3>(), st>>>(A);
+      else adjoint_x_kernel<T, 3, kAdjWrite><<<grid, kXThreads, adj_x_smem<T, 3>(), st>>>(A);
+      break;
+    case 4:
+      if (c.combine) adjoint_x_kernel<T, 4, kAdjCombine><<<grid, kXThreads, adj_x_smem<T, 4>(), st>>>(A);
+      else adjoint_x_kernel<T, 4, kAdjWrite><<<grid, kXThreads, adj_x_smem<T, 4>(), st>>>(A);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_y(const GridInfo& g, const Scheme& s, const AdjCall<T>& c, cudaStream_t st) {
+  if (g.nvar != 4) return cudaErrorInvalidValue;
+  AdjArgs<T> A = make_adj_args<T>(g, s, 1, c);
+  dim3 grid((unsigned)((g.nx + kAYCols - 1) / kAYCols), (unsigned)((g.ny + kAYTile - 1) / kAYTile));
+  dim3 block(kAYCols, kAYRowsT);
+  adjoint_y_kernel<T, 4><<<grid, block, adj_y_smem<T, 4>(), st>>>(A);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st) {
   SweepArgs<T> A = make_args<T>(g, s, 0, c);
   switch (g.nvar) {
-    case 1: return c.stage ? run_sweep_x<T, 1, kStage>(g, A, st) : run_sweep_x<T, 1, kWriteL>(g, A, st);
-    case 3: return c.stage ? run_sweep_x<T, 3, kStage>(g, A, st) : run_sweep_x<T, 3, kWriteL>(g, A, st);
-    case 4: return c.stage ? run_sweep_x<T, 4, kStage>(g, A, st) : run_sweep_x<T, 4, kWriteL>(g, A, st);
+    case 1: return c.stage ? run_sweep_x<T, 1, kStage>(g, A, false, st) : run_sweep_x<T, 1, kWriteL>(g, A, false, st);
+    case 3: {
+      const bool f = use_fixed<3>(s);
+      return c.stage ? run_sweep_x<T, 3, kStage>(g, A, f, st) : run_sweep_x<T, 3, kWriteL>(g, A, f, st);
+    }
+    case 4: {
+      const bool f = use_fixed<4>(s);
+      return c.stage ? run_sweep_x<T, 4, kStage>(g, A, f, st) : run_sweep_x<T, 4, kWriteL>(g, A, f, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -74,8 +164,11 @@ template <typename T>
 cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st) {
   SweepArgs<T> A = make_args<T>(g, s, 1, c);
   switch (g.nvar) {
-    case 1: return c.stage ? run_sweep_y<T, 1, kStage>(g, A, st) : run_sweep_y<T, 1, kWriteL>(g, A, st);
-    case 4: return c.stage ? run_sweep_y<T, 4, kStage>(g, A, st) : run_sweep_y<T, 4, kWriteL>(g, A, st);
+    case 1: return c.stage ? run_sweep_y<T, 1, kStage>(g, A, false, st) : run_sweep_y<T, 1, kWriteL>(g, A, false, st);
+    case 4: {
+      const bool f = use_fixed<4>(s);
+      return c.stage ? run_sweep_y<T, 4, kStage>(g, A, f, st) : run_sweep_y<T, 4, kWriteL>(g, A, f, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -129,6 +222,10 @@ cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int w
                                          cudaStream_t);                                              \
   template cudaError_t launch_sweep_y<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
                                          cudaStream_t);                                              \
+  template cudaError_t launch_adjoint_x<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
+                                           cudaStream_t);                                            \
+  template cudaError_t launch_adjoint_y<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
+                                           cudaStream_t);                                            \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
   template cudaError_t launch_reduce<T>(const GridInfo&, const void*, const void*, int, double*, int, \
                                         unsigned int*, double*, cudaStream_t);                       \

@@ -88,3 +88,17 @@ def test_init_rejects_bad_params_without_gpu(lib):
     p = lib.make_params(lib.WCNS_EULER, lib.WCNS_F32, weights="JS")
     with pytest.raises(lib.WcnsError):
         lib.wcns_init(g32, p)
+
+
+def test_batch_init_rejects_bad_layout_without_gpu(lib):
+    import numpy as np
+    p = lib.make_params(lib.WCNS_EULER, lib.WCNS_F64)
+    for offs, sizes, total in (([0, 50], [100, 100], 200),   # overlapping problems
+                               ([0, 150], [100, 100], 200),  # past the end
+                               ([0], [0], 10)):              # empty problem
+        with pytest.raises(lib.WcnsError) as e:
+            lib.wcns_batch_init(np.array(offs), np.array(sizes), total, 0.0, 1.0, 1, p, lib.WCNS_F64)
+        assert e.value.status == lib.WCNS_ERR_ARG
+    with pytest.raises(lib.WcnsError) as e:
+        lib.wcns_batch_init(np.array([0]), np.array([10]), 10, 0.0, 1.0, 1, p, lib.WCNS_F64, tile=100)
+    assert e.value.status == lib.WCNS_ERR_ARG
