@@ -145,6 +145,27 @@ wcns_status wcns_get_time(wcns_ctx* ctx, double* t, int64_t* steps_taken);
  * Accumulation is FP64 for both element types. */
 wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t what, double* out);
 
+/* The reductions of wcns_reduce (SUM, L1, LINF only) without a context and without
+ * any device allocation.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc where they need the reduction -- a loop that reserved all of
+ * its device memory up front and must not stall the device, or code inside a
+ * framework whose allocator owns the device memory -- and therefore cannot create a
+ * wcns_ctx either.  Its scratch is one 64 KiB array in device memory that every GPU
+ * loading the library holds until the process exits.
+ *   grid:   layout of a and b (nvar <= 4; dtype, nx, ny, pitch as for wcns_init;
+ *           lo/hi/bc are ignored).  nvar > 4 returns WCNS_ERR_ARG.
+ *   a, b:   device grid buffers (b may be NULL: |a|); 16-byte aligned.
+ *   what:   WCNS_REDUCE_SUM, _L1 or _LINF (else WCNS_ERR_UNSUPPORTED).
+ *   stream: cudaStream_t the work is enqueued on (NULL: default stream).
+ *   out:    DEVICE buffer of nvar doubles owned by the caller; written asynchronously.
+ * The first call on a device resolves the array's device address (a CUDA runtime
+ * query) with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: each call clears
+ * the counters it needs on its own stream.  Calls that overlap on the GPU (unordered
+ * streams) race on the array and give wrong results. */
+wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void* b, int32_t what,
+                                void* stream, double* out);
+
 /* Adjoint of one TVD-RK3 step of fixed size dt > 0 (the benchmark spec's hand-written
  * adjoint of steps (a)-(e)): given the checkpoint u_n and the cotangent lam_np1 of
  * u_{n+1} = S(u_n), writes lam_n = (dS/du_n)^T lam_np1.  The stage states u1, u2 are

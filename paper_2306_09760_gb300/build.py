@@ -28,6 +28,7 @@ FAST_F32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 UNITS = {
     "wcns_api.cu": [],
     "wcns_batch.cu": FAST_F32,
+    "wcns_noalloc.cu": [],
     "wcns_f64.cu": [],
     "wcns_f32.cu": FAST_F32,
 }

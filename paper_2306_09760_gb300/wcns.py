@@ -75,6 +75,7 @@ def load():
         "wcns_get_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "wcns_reduce": (st, [vp, vp, vp, ctypes.c_int32, P(ctypes.c_double)]),
         "wcns_adjoint_step": (st, [vp, vp, ctypes.c_double, vp, vp]),
+        "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
         "wcns_status_string": (ctypes.c_char_p, [st]),
         "wcns_profile_enable": (st, [vp, ctypes.c_int32]),
@@ -171,6 +172,12 @@ def wcns_reduce(ctx, a, b, what: int, nout: int) -> np.ndarray:
     _check(load().wcns_reduce(ctx, _ptr(a), _ptr(b), int(what), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
            "wcns_reduce")
     return out[:nout]
+
+
+def wcns_reduce_noalloc(grid: wcns_grid, a, b, what: int, out_dev, stream=None):
+    """Context-free, allocation-free reduction; `out_dev` is a device buffer of nvar doubles."""
+    _check(load().wcns_reduce_noalloc(ctypes.byref(grid), _ptr(a), _ptr(b), int(what), _stream_handle(stream),
+                                      _ptr(out_dev)), "wcns_reduce_noalloc")
 
 
 def wcns_adjoint_step(ctx, u_n, dt: float, lam_np1, lam_n):
