@@ -421,7 +421,12 @@ def run_batched_variant(W, torch, inputs, hbm_peak, steps=10):
             "status": W.wcns_status_string(st), "hbm_frac": rate * 1e6 * 96 / 1e9 / hbm_peak}
 
 
-ADJ_PARAMS = dict(flux="LLF_FROZEN", xi=100.0, zp=2, characteristic=False)
+# Adjoint configuration: frozen-alpha LLF (a smooth flux), FE map at xi = 100, Z exponent 2
+# (no |IS0 - IS2| kink), characteristic projection, eps = 1e-4.  With eps = 1e-40 the
+# weights' derivatives in near-constant data are O(1/eps) and the tangent of this noisy
+# workload grows by 1e5-1e9 over 40 steps, so its gradient is not defined at practical
+# scales; eps of the order of the noise's IS keeps the 200-step tangent bounded (~0.9).
+ADJ_PARAMS = dict(flux="LLF_FROZEN", xi=100.0, zp=2, characteristic=True, eps=1e-4)
 
 
 def adjoint_problem(inputs, n=512, seed=0):

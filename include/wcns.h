@@ -66,6 +66,9 @@ enum { WCNS_W_JS = 0, WCNS_W_Z = 1, WCNS_W_FE = 2, WCNS_W_PFE = 3, WCNS_W_M = 4 
  * Lax-Friedrichs with a frozen dissipation speed alpha[d] (smooth; for adjoints). */
 enum { WCNS_FLUX_LLF = 0, WCNS_FLUX_ROE = 1, WCNS_FLUX_HLLC = 2, WCNS_FLUX_LLF_FROZEN = 3 };
 enum { WCNS_REDUCE_SUM = 0, WCNS_REDUCE_L1 = 1, WCNS_REDUCE_LINF = 2, WCNS_REDUCE_MAXWAVE = 3 };
+/* Time integrator: third-order TVD Runge-Kutta (Shu-Osher form; default) or the
+ * classical fourth-order Runge-Kutta the paper uses, in the form printed as Eq. 16. */
+enum { WCNS_RK3 = 0, WCNS_RK4 = 1 };
 
 /* Grid descriptor (Sec. 2: uniform cells, h = (hi - lo) / n per direction). */
 typedef struct {
@@ -73,7 +76,8 @@ typedef struct {
   int32_t nvar;      /* 1 (advection), 3 (Euler, ndim 1), 4 (Euler, ndim 2) */
   int32_t dtype;     /* WCNS_F64 or WCNS_F32 */
   int32_t reserved;  /* must be 0 */
-  int64_t nx, ny;    /* cells; ny = 1 when ndim = 1; 1 <= nx, ny <= 2^26 */
+  int64_t nx, ny;    /* cells; 1 <= nx, ny <= 2^26.  ndim = 1 with ny > 1 holds ny
+                        independent lines of nx cells (no coupling between rows). */
   int64_t pitch;     /* elements per row; pitch >= nx and pitch % 32 == 0 */
   double lo[2], hi[2];
   int32_t bc[2];     /* WCNS_BC_* for x and y */
@@ -87,7 +91,8 @@ typedef struct {
   int32_t characteristic;  /* 1: interpolate characteristic variables (default); 0: conserved */
   int32_t z_p;             /* Z-weight exponent p of Eq. 14, 1 or 2; default 1 */
   int32_t renorm;          /* 1: renormalise the mapped weights (default) */
-  int32_t reserved[2];     /* must be 0 */
+  int32_t integrator;      /* WCNS_RK3 (default) or WCNS_RK4 (wcns_step only) */
+  int32_t reserved;        /* must be 0 */
   double adv_speed[2];     /* advection speed per direction (advection only) */
   double gamma;            /* ratio of specific heats; default 1.4 */
   double eps;              /* epsilon of Eq. 11 / Eq. 14; default 1e-40 (F64), 1e-30 (F32) */
@@ -119,7 +124,9 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
 wcns_status wcns_rhs(wcns_ctx* ctx, const void* u, void* dudt);
 
 /* Advances u in place by nsteps TVD-RK3 steps (Shu-Osher form):
- *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),  u <- 1/3 u + 2/3 (u2 + dt L(u2)).
+ *   u1 = u + dt L(u),  u2 = 3/4 u + 1/4 (u1 + dt L(u1)),  u <- 1/3 u + 2/3 (u2 + dt L(u2)),
+ * or, with integrator WCNS_RK4, classical RK4 steps written as in Eq. 16 (one more
+ * stage state of scratch, allocated by wcns_init).
  * dt > 0: fixed step.  dt <= 0: each step takes dt = cfl / sum_d(max(|u_d| + c) / h_d)
  * (advection: |a_d| for max(|u_d| + c)), reduced on the device, never read back.
  * t_end > 0: each step is clipped so the device time t never passes t_end; once t

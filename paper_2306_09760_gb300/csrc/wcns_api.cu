@@ -21,6 +21,7 @@ struct wcns_ctx {
   size_t nelem;          // elements of one grid buffer (nvar * ny * pitch)
   void* u1;              // stage states
   void* u2;
+  void* u3;              // third stage state (RK4 only)
   void* R;               // L_x planes (2D)
   void* host_state;      // device copy used by wcns_step_host (lazy)
   void* adj1;            // adjoint stage cotangents (lazy)
@@ -79,7 +80,8 @@ wcns_status check_params(const wcns_params* p, int dtype, int nvar, int ndim) {
   if (p->weights < WCNS_W_JS || p->weights > WCNS_W_M) return WCNS_ERR_ARG;
   if (p->flux < WCNS_FLUX_LLF || p->flux > WCNS_FLUX_LLF_FROZEN) return WCNS_ERR_ARG;
   if (p->z_p != 1 && p->z_p != 2) return WCNS_ERR_ARG;
-  if (p->reserved[0] || p->reserved[1]) return WCNS_ERR_ARG;
+  if (p->integrator != WCNS_RK3 && p->integrator != WCNS_RK4) return WCNS_ERR_ARG;
+  if (p->reserved) return WCNS_ERR_ARG;
   if (!(p->eps > 0.0) || !(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->xi > 0.0)) return WCNS_ERR_ARG;
   if (!(p->kappa > 0.0) || p->cv < 0.0) return WCNS_ERR_ARG;
   // in single precision eps^2 must stay a normal number for the JS and M weights
@@ -135,24 +137,41 @@ cudaError_t timed(wcns_ctx* c, int kind, F f) {
   return cudaEventRecord(ev.b, c->stream);
 }
 
+// Stage coefficients: TVD-RK3 form out = a*un + b*(u + dt*L), or (general) the form
+// out = a*un + b*u + e*dt*L + c1*X1 + c2*X2.
+struct StageCoef {
+  double a, b;
+  bool general;
+  double e, c1, c2;
+  const void* X1;
+  const void* X2;
+};
+
 template <typename T>
-cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool stage_mode, double a, double b) {
+cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool stage_mode, const StageCoef& k) {
   SweepCall<T> x{};
   x.u = static_cast<const T*>(u);
   x.fallbacks = c->d_fallbacks;
+  x.general = k.general;
+  x.e = k.e; x.c1 = k.c1; x.c2 = k.c2;
+  x.X1 = static_cast<const T*>(k.X1);
+  x.X2 = static_cast<const T*>(k.X2);
   if (c->g.ndim == 1) {
     x.un = static_cast<const T*>(un);
     x.out = static_cast<T*>(out);
     x.dt = stage_mode ? c->d_dt : nullptr;
-    x.a = a; x.b = b;
+    x.a = k.a; x.b = k.b;
     x.stage = stage_mode;
     return timed(c, stage_mode ? kProfSweepXStage1D : kProfSweepXRhs,
                  [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
   }
-  // 2D: L_x into R (skipped when dt == 0 in stage mode), then y sweep + stage
+  // 2D: the x sweep writes L_x (RHS) or the partial stage (all terms but the y part of L)
+  // into R (skipped when dt == 0), then the y sweep adds L_y or its stage multiple.
   x.out = static_cast<T*>(c->R);
   x.dt = stage_mode ? c->d_dt : nullptr;
-  x.stage = false;
+  x.un = static_cast<const T*>(un);
+  x.a = k.a; x.b = k.b;
+  x.stage = stage_mode;
   cudaError_t e = timed(c, stage_mode ? kProfSweepXLx : kProfSweepXRhs,
                         [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
   if (e != cudaSuccess) return e;
@@ -162,7 +181,9 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   y.R = static_cast<const T*>(c->R);
   y.out = static_cast<T*>(out);
   y.dt = stage_mode ? c->d_dt : nullptr;
-  y.a = a; y.b = b;
+  y.a = k.a; y.b = k.b;
+  y.general = k.general;
+  y.e = k.e;
   y.stage = stage_mode;
   y.fallbacks = c->d_fallbacks;
   return timed(c, stage_mode ? kProfSweepYStage : kProfSweepYRhs,
@@ -170,13 +191,20 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
 }
 
 cudaError_t rhs_into(wcns_ctx* c, const void* u, void* out) {
-  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, nullptr, out, false, 0.0, 1.0); },
-                 [&] { return sweeps<float>(c, u, nullptr, out, false, 0.0, 1.0); });
+  StageCoef k{0.0, 1.0, false, 0.0, 0.0, 0.0, nullptr, nullptr};
+  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, nullptr, out, false, k); },
+                 [&] { return sweeps<float>(c, u, nullptr, out, false, k); });
 }
 
+cudaError_t stage_coef(wcns_ctx* c, const void* u, const void* un, void* out, const StageCoef& k) {
+  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, un, out, true, k); },
+                 [&] { return sweeps<float>(c, u, un, out, true, k); });
+}
+
+// TVD-RK3 stage out = a*un + b*(u + dt*L(u)).
 cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b) {
-  return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, un, out, true, a, b); },
-                 [&] { return sweeps<float>(c, u, un, out, true, a, b); });
+  StageCoef k{a, b, false, 0.0, 0.0, 0.0, nullptr, nullptr};
+  return stage_coef(c, u, un, out, k);
 }
 
 cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool maxwave_only) {
@@ -227,10 +255,23 @@ cudaError_t adjoint_stage(wcns_ctx* c, const void* u, const void* mu, const void
   return timed(c, kProfAdjY, [&] { return launch_adjoint_y<T>(c->gi, c->s, a, c->stream); });
 }
 
-// One TVD-RK3 step on u in place (Shu-Osher form).
+// One TVD-RK3 step on u in place (Shu-Osher form), or one classical RK4 step in the
+// form printed as Eq. 16:
+//   u1 = u + dt/2 L(u), u2 = u + dt/2 L(u1), u3 = u + dt L(u2),
+//   u' = -u/3 + u1/3 + 2 u2/3 + u3/3 + dt/6 L(u3).
 cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) {
   cudaError_t e;
   if ((e = dt_launch(c, u, dt, t_end, false)) != cudaSuccess) return e;
+  if (c->p.integrator == WCNS_RK4) {
+    StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr};
+    if ((e = stage_coef(c, u, u, c->u1, k1)) != cudaSuccess) return e;
+    StageCoef k2{1.0, 0.0, true, 0.5, 0.0, 0.0, nullptr, nullptr};
+    if ((e = stage_coef(c, c->u1, u, c->u2, k2)) != cudaSuccess) return e;
+    StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr};
+    if ((e = stage_coef(c, c->u2, u, c->u3, k3)) != cudaSuccess) return e;
+    StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2};
+    return stage_coef(c, c->u3, u, u, k4);
+  }
   if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0)) != cudaSuccess) return e;
   if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25)) != cudaSuccess) return e;
   return stage(c, c->u2, u, u, 1.0 / 3.0, 2.0 / 3.0);
@@ -315,8 +356,8 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   if (g.reserved != 0) return WCNS_ERR_ARG;
   const int64_t kMaxN = (int64_t)1 << 26;
   if (g.nx < 1 || g.ny < 1 || g.nx > kMaxN || g.ny > kMaxN) return WCNS_ERR_ARG;
-  if (g.ndim == 1 && g.ny != 1) return WCNS_ERR_ARG;
-  if (g.ny > 65535 * (int64_t)59 || (g.ndim == 1 && g.ny > 65535)) return WCNS_ERR_ARG;
+  // ndim 1 with ny > 1: ny independent lines of nx cells (rows are not coupled)
+  if (g.ny > 65535 * (int64_t)43 || (g.ndim == 1 && g.ny > 65535)) return WCNS_ERR_ARG;
   if (g.pitch < g.nx || g.pitch % 32 != 0) return WCNS_ERR_ARG;
   if ((double)g.nvar * (double)g.ny * (double)g.pitch > 4.0e9) return WCNS_ERR_ARG;
   for (int d = 0; d < g.ndim; ++d) {
@@ -351,6 +392,7 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   if (e == cudaSuccess) e = cudaMalloc(&c->u1, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->u2, bytes);
   if (e == cudaSuccess && g.ndim == 2) e = cudaMalloc(&c->R, bytes);
+  if (e == cudaSuccess && params->integrator == WCNS_RK4) e = cudaMalloc(&c->u3, bytes);
   const size_t scal_bytes = 4096 + sizeof(double) * 2 * kMaxRedBlocks;
   if (e == cudaSuccess) e = cudaMalloc(&c->scal, scal_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->scal, 0, scal_bytes, c->stream);
@@ -457,7 +499,9 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
     return WCNS_ERR_ARG;
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
   const wcns_params& p = c->p;
-  if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M) return WCNS_ERR_UNSUPPORTED;
+  if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M ||
+      p.integrator != WCNS_RK3)
+    return WCNS_ERR_UNSUPPORTED;
   const size_t bytes = c->nelem * c->elem;
   if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
   if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
@@ -534,6 +578,7 @@ void wcns_destroy(wcns_ctx* c) {
   drop_graph(c);
   if (c->u1) cudaFree(c->u1);
   if (c->u2) cudaFree(c->u2);
+  if (c->u3) cudaFree(c->u3);
   if (c->R) cudaFree(c->R);
   if (c->host_state) cudaFree(c->host_state);
   if (c->adj1) cudaFree(c->adj1);

@@ -292,7 +292,7 @@ wcns_status wcns_batch_init(const int64_t* offsets, const int64_t* n, int32_t np
   if (bc != WCNS_BC_PERIODIC && bc != WCNS_BC_TRANSMISSIVE) return WCNS_ERR_ARG;
   if (dtype != WCNS_F64 && dtype != WCNS_F32) return WCNS_ERR_ARG;
   if (tile != 0 && tile != 123 && tile != 251 && tile != 507) return WCNS_ERR_ARG;
-  if (params->system != WCNS_EULER) return WCNS_ERR_UNSUPPORTED;
+  if (params->system != WCNS_EULER || params->integrator != WCNS_RK3) return WCNS_ERR_UNSUPPORTED;
   if (params->weights < WCNS_W_JS || params->weights > WCNS_W_M || params->flux < WCNS_FLUX_LLF ||
       params->flux > WCNS_FLUX_LLF_FROZEN || (params->z_p != 1 && params->z_p != 2) || !(params->eps > 0.0) ||
       !(params->gamma > 1.0) || !(params->cfl > 0.0))

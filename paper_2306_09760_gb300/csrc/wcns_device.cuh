@@ -36,6 +36,7 @@ struct Scheme {
 template <typename T>
 struct SchemeT {
   int system, weights, flux, characteristic, zp, renorm;
+  int xi_small;  // single precision with xi < 1e4: the FE map uses the exponential form of tanh
   T gamma, gm1, eps, xi, cv, harten;
   T speed[2];
   T null0[3], null1[4], null2[3];
@@ -45,6 +46,7 @@ template <typename T>
 inline SchemeT<T> scheme_as(const Scheme& s) {
   SchemeT<T> r;
   r.system = s.system; r.weights = s.weights; r.flux = s.flux;
+  r.xi_small = (sizeof(T) == 4 && s.xi < 1e4) ? 1 : 0;
   r.characteristic = s.characteristic; r.zp = s.zp; r.renorm = s.renorm;
   r.gamma = T(s.gamma); r.gm1 = T(s.gamma - 1.0); r.eps = T(s.eps); r.xi = T(s.xi);
   r.cv = T(s.cv); r.harten = T(s.harten);
@@ -179,8 +181,35 @@ WCNS_HD T side_of(T w, T n) { return w > n ? T(1) : T(-1); }
 // Eq. 20 for weight i.  When every tanh argument is saturated (the usual case at
 // large xi) each term is exactly +-amplitude and the map is evaluated with signs;
 // otherwise the exact out-of-line path runs.  Both give the same value there.
+// tanh(z) = 1 - 2 / (e^{2z} + 1) (Eq. 19 rearranged), evaluated with the fast exponential
+// and reciprocal of the single-precision pipe; it reaches +-1 exactly for large |z|
+// (e^{2z} overflows to inf or underflows to 0), so no branch is needed.  Absolute error
+// about 1e-7, well inside the single-precision path's tolerance.
+WCNS_HD float tanh_expf(float z) {
+#ifdef __CUDA_ARCH__
+  return 1.0f - __fdividef(2.0f, __expf(2.0f * z) + 1.0f);
+#else
+  return tanhf(z);
+#endif
+}
+
+// Eq. 20 for the single-precision path at moderate xi (every term evaluated).
+template <typename T, int K>
+WCNS_HD T fe_map_expf(T w, const T (&n)[K], const T (&amp)[K + 1], T xi) {
+  T acc = T(0);
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc = acc + amp[j] * tanh_expf(xi * (w - n[j]));
+  return acc;
+}
+
 template <typename T>
 WCNS_HD T fe_map0(T w, const SchemeT<T>& s) {
+  if constexpr (sizeof(T) == 4) {
+    if (s.xi_small) {
+      const T amp[4] = {(T(1.0 / 16.0) - w) / T(2), T(1.0 / 6.0 - 1.0 / 16.0) / T(2), (w - T(1.0 / 6.0)) / T(2), T(0)};
+      return fe_map_expf<T, 3>(w, s.null0, amp, s.xi) + w;
+    }
+  }
   if (!all_saturated<T, 3>(w, s.null0, s.xi)) return fe_map_slow<T>(0, w, s);
   T acc = ((T(1.0 / 16.0) - w) / T(2)) * side_of(w, s.null0[0]);
   acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * side_of(w, s.null0[1]);
@@ -189,6 +218,13 @@ WCNS_HD T fe_map0(T w, const SchemeT<T>& s) {
 }
 template <typename T>
 WCNS_HD T fe_map1(T w, const SchemeT<T>& s) {
+  if constexpr (sizeof(T) == 4) {
+    if (s.xi_small) {
+      const T amp[5] = {(T(10.0 / 16.0) - w) / T(2), T(1.0 / 2.0 - 10.0 / 16.0) / T(2),
+                        T(5.0 / 6.0 - 1.0 / 2.0) / T(2), (w - T(5.0 / 6.0)) / T(2), T(0)};
+      return fe_map_expf<T, 4>(w, s.null1, amp, s.xi) + w;
+    }
+  }
   if (!all_saturated<T, 4>(w, s.null1, s.xi)) return fe_map_slow<T>(1, w, s);
   T acc = ((T(10.0 / 16.0) - w) / T(2)) * side_of(w, s.null1[0]);
   acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * side_of(w, s.null1[1]);
@@ -198,11 +234,64 @@ WCNS_HD T fe_map1(T w, const SchemeT<T>& s) {
 }
 template <typename T>
 WCNS_HD T fe_map2(T w, const SchemeT<T>& s) {
+  if constexpr (sizeof(T) == 4) {
+    if (s.xi_small) {
+      const T amp[4] = {(T(5.0 / 16.0) - w) / T(2), T(1.0 / 2.0 - 5.0 / 16.0) / T(2), (w - T(1.0 / 2.0)) / T(2), T(0)};
+      return fe_map_expf<T, 3>(w, s.null2, amp, s.xi) + w;
+    }
+  }
   if (!all_saturated<T, 3>(w, s.null2, s.xi)) return fe_map_slow<T>(2, w, s);
   T acc = ((T(5.0 / 16.0) - w) / T(2)) * side_of(w, s.null2[0]);
   acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * side_of(w, s.null2[1]);
   acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * side_of(w, s.null2[2]);
   return acc + w;
+}
+
+// Eq. 20 for the three weights together.  Where every tanh argument of all three maps
+// is saturated (|xi (w - n)| >= kSat for each null point n), each term is exactly
+// +-amplitude and the sum collapses to a staircase: the identity below the first and
+// above the last null point, the control values of Table 1 in between.  That is
+// evaluated by comparisons; otherwise (any argument unsaturated) the exact path runs.
+template <typename T>
+WCNS_HD T null_distance(T w, const T* n, int k) {
+  T d = Num<T>::abs_(w - n[0]);
+  for (int j = 1; j < k; ++j) d = fmin(d, Num<T>::abs_(w - n[j]));
+  return d;
+}
+
+template <typename T>
+WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
+  bool sat;
+  if constexpr (sizeof(T) == 8) {
+    // the distance test in single precision, with a margin for the rounding to float
+    const float xf = (float)s.xi;
+    const float a = (float)w0, b = (float)w1, c = (float)w2;
+    float d = fminf(fminf(fabsf(a - (float)s.null0[0]), fabsf(a - (float)s.null0[1])), fabsf(a - (float)s.null0[2]));
+    d = fminf(d, fminf(fminf(fabsf(b - (float)s.null1[0]), fabsf(b - (float)s.null1[1])),
+                       fminf(fabsf(b - (float)s.null1[2]), fabsf(b - (float)s.null1[3]))));
+    d = fminf(d, fminf(fminf(fabsf(c - (float)s.null2[0]), fabsf(c - (float)s.null2[1])), fabsf(c - (float)s.null2[2])));
+    sat = xf * d >= 20.0f + 1.0e-4f + 4.0e-7f * xf;
+  } else {
+    if (s.xi_small) {
+      w0 = fe_map0<T>(w0, s); w1 = fe_map1<T>(w1, s); w2 = fe_map2<T>(w2, s);
+      return;
+    }
+    T d = fmin(fmin(fmin(Num<T>::abs_(w0 - s.null0[0]), Num<T>::abs_(w0 - s.null0[1])), Num<T>::abs_(w0 - s.null0[2])),
+               fmin(fmin(Num<T>::abs_(w1 - s.null1[0]), Num<T>::abs_(w1 - s.null1[1])),
+                    fmin(Num<T>::abs_(w1 - s.null1[2]), Num<T>::abs_(w1 - s.null1[3]))));
+    d = fmin(d, fmin(fmin(Num<T>::abs_(w2 - s.null2[0]), Num<T>::abs_(w2 - s.null2[1])), Num<T>::abs_(w2 - s.null2[2])));
+    sat = s.xi * d >= Num<T>::kSat;
+  }
+  if (!sat) {
+    w0 = fe_map_slow<T>(0, w0, s); w1 = fe_map_slow<T>(1, w1, s); w2 = fe_map_slow<T>(2, w2, s);
+    return;
+  }
+  const T g0 = (w0 < s.null0[1]) ? T(1.0 / 16.0) : T(1.0 / 6.0);
+  w0 = (w0 < s.null0[0] || w0 > s.null0[2]) ? w0 : g0;
+  const T g1 = (w1 < s.null1[1]) ? T(10.0 / 16.0) : ((w1 < s.null1[2]) ? T(1.0 / 2.0) : T(5.0 / 6.0));
+  w1 = (w1 < s.null1[0] || w1 > s.null1[3]) ? w1 : g1;
+  const T g2 = (w2 < s.null2[1]) ? T(5.0 / 16.0) : T(1.0 / 2.0);
+  w2 = (w2 < s.null2[0] || w2 > s.null2[2]) ? w2 : g2;
 }
 
 // Eq. 13: Henrick's mapping of a JS weight with ideal value d.
@@ -219,10 +308,10 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
   const int zp = WCNS_OPT(FIX, s, zp);
   const int renorm = WCNS_OPT(FIX, s, renorm);
   const T d0 = T(1.0 / 16.0), d1 = T(10.0 / 16.0), d2 = T(5.0 / 16.0);
-  // Eq. 5
-  T q0 = (T(3) * v0 - T(10) * v1 + T(15) * v2) / T(8);
-  T q1 = (-v1 + T(6) * v2 + T(3) * v3) / T(8);
-  T q2 = (T(3) * v2 + T(6) * v3 - v4) / T(8);
+  // Eq. 5 (coefficients divided by 8 beforehand; powers of two, so exactly)
+  T q0 = T(0.375) * v0 - T(1.25) * v1 + T(1.875) * v2;
+  T q1 = -T(0.125) * v1 + T(0.75) * v2 + T(0.375) * v3;
+  T q2 = T(0.375) * v2 + T(0.75) * v3 - T(0.125) * v4;
   // Eq. 10 scaled by h and h^2, then Eq. 9
   T f0 = (v0 - T(4) * v1 + T(3) * v2) / T(2), s0 = v0 - T(2) * v1 + v2;
   T f1 = (v3 - v1) / T(2), s1 = v1 - T(2) * v2 + v3;
@@ -270,7 +359,8 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
       }
       if (!keep) {
         // Eq. 20 on each weight, then renormalised
-        T g0 = fe_map0<T>(w0, s), g1 = fe_map1<T>(w1, s), g2 = fe_map2<T>(w2, s);
+        T g0 = w0, g1 = w1, g2 = w2;
+        fe_map_all<T>(g0, g1, g2, s);
         if (renorm) {
           const T isg = T(1) / (g0 + g1 + g2);
           w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;

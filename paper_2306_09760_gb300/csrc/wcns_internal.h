@@ -34,6 +34,11 @@ struct SweepCall {
   double a, b;
   bool stage;  // apply the RK stage update (else write L)
   unsigned long long* fallbacks;
+  // general stage form out = a*un + b*u + e*dt*L + c1*X1 + c2*X2 (RK4); else TVD-RK3 form
+  bool general;
+  double e, c1, c2;
+  const T* X1;
+  const T* X2;
 };
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);

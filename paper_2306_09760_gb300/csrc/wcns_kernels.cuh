@@ -27,6 +27,12 @@ struct SweepArgs {
   T* out;              // destination (L, L_x or the stage state)
   const double* dt;    // device step (stage modes)
   T a, b;
+  // General stage form (RK4, Eq. 16): out = a*un + b*u + e*dt*L + c1*X1 + c2*X2.
+  // When `general` is 0 the TVD-RK3 form a*un + b*(u + dt*L) is used as written.
+  int general;
+  T e, c1, c2;
+  const T* X1;
+  const T* X2;
   int64_t nx, ny, pitch, fstride;  // fstride = ny * pitch (elements per variable plane)
   int bc;              // boundary of this sweep's direction
   T inv_h;
@@ -34,6 +40,9 @@ struct SweepArgs {
   unsigned long long* fallbacks;   // interfaces that fell back to first order
 };
 
+// kWriteL: out = L (or L_x).  kStage: out = a*un + b*(u + dt*L).  In a 2D stage the x
+// sweep runs in kStage form with L_x and writes the partial stage into R; the y sweep
+// then adds b*dt*L_y, so its epilogue reads one array instead of two.
 enum SweepMode { kWriteL = 0, kStage = 1 };
 
 __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
@@ -66,6 +75,14 @@ __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
   const int64_t c0 = (int64_t)blockIdx.x * kXTile;
   const int ntile = (int)min((int64_t)kXTile, A.nx - c0);
   const T* base = A.u + row * A.pitch;
+  // u^n of this thread's output cell, loaded now so the latency hides under the sweep
+  T unv[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) unv[k] = T(0);
+  if (MODE == kStage && A.a != T(0) && (int)threadIdx.x < ntile) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) unv[k] = A.un[k * A.fstride + row * A.pitch + c0 + threadIdx.x];
+  }
   for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
     const int v = idx / kXCells, s = idx - v * kXCells;
     if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
@@ -99,8 +116,15 @@ __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
         A.out[k * A.fstride + off] = L;
       } else {
         T cur = su[k * kXCells + t + 5];
-        T v = A.b * (cur + dt * L);
-        if (A.a != T(0)) v = A.a * A.un[k * A.fstride + off] + v;
+        T v;
+        if (!A.general) {
+          v = A.b * (cur + dt * L);
+          if (A.a != T(0)) v = A.a * unv[k] + v;
+        } else {
+          v = A.a * unv[k] + A.b * cur + (A.e * dt) * L;
+          if (A.X1) v = v + A.c1 * A.X1[k * A.fstride + off];
+          if (A.X2) v = v + A.c2 * A.X2[k * A.fstride + off];
+        }
         A.out[k * A.fstride + off] = v;
       }
     }
@@ -108,15 +132,16 @@ __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
-// y sweep: one block per (32 columns, YT rows); 32 x 8 threads, each thread
-// computes 8 interfaces of its column.  L = L_x (from R) + L_y.
+// y sweep: one block per (32 columns, kYTile rows); 32 x 8 threads, each thread
+// computes kYPer interfaces of its column.  Stage: out = R + b*dt*L_y with R the
+// partial stage of the x sweep; RHS: out = R + L_y with R = L_x.
 // ---------------------------------------------------------------------------
 constexpr int kYCols = 32;
 constexpr int kYRowsT = 8;                 // thread rows
-constexpr int kYPer = 8;                   // interfaces per thread
-constexpr int kYIfc = kYRowsT * kYPer;     // 64 interfaces per column
-constexpr int kYTile = kYIfc - 5;          // 59 output rows per block
-constexpr int kYCells = kYIfc + 5;         // 69 staged rows
+constexpr int kYPer = 6;                   // interfaces per thread
+constexpr int kYIfc = kYRowsT * kYPer;     // 48 interfaces per column
+constexpr int kYTile = kYIfc - 5;          // 43 output rows per block
+constexpr int kYCells = kYIfc + 5;         // 53 staged rows (52 KB FP32: four blocks per SM)
 
 template <typename T, int NV>
 constexpr size_t sweep_y_smem() { return sizeof(T) * NV * (kYCells + kYIfc) * kYCols; }
@@ -175,25 +200,29 @@ __global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> 
     count_fallbacks(fb, A.fallbacks);
   }
   __syncthreads();
-  if (tx < ncol) {
-    for (int q = 0; q < kYPer; ++q) {
-      const int t = threadIdx.y + kYRowsT * q;
-      if (t >= ntile) break;
+  // epilogue: all loads of R first (one latency per block), then the sums
+  T rv[kYPer][NV];
+#pragma unroll
+  for (int q = 0; q < kYPer; ++q) {
+    const int t = threadIdx.y + kYRowsT * q;
+    const bool on = tx < ncol && t < ntile;
+    const int64_t off = (r0 + t) * A.pitch + c0 + tx;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) rv[q][k] = on ? A.R[k * A.fstride + off] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < kYPer; ++q) {
+    const int t = threadIdx.y + kYRowsT * q;
+    if (tx < ncol && t < ntile) {
       const int64_t off = (r0 + t) * A.pitch + c0 + tx;
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const T* f = sf + (k * kYIfc + t) * kYCols + tx;
         T Ly = flux_difference<T>(f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
                                   f[5 * kYCols], A.inv_h);
-        T L = A.R[k * A.fstride + off] + Ly;
-        if (MODE == kWriteL) {
-          A.out[k * A.fstride + off] = L;
-        } else {
-          T cur = su[(k * kYCells + t + 5) * kYCols + tx];
-          T v = A.b * (cur + dt * L);
-          if (A.a != T(0)) v = A.a * A.un[k * A.fstride + off] + v;
-          A.out[k * A.fstride + off] = v;
-        }
+        // RHS: R = L_x.  Stage: R = a*un + b*(u + dt*L_x) from the x sweep.
+        A.out[k * A.fstride + off] =
+            (MODE == kWriteL) ? rv[q][k] + Ly : rv[q][k] + ((A.general ? A.e : A.b) * dt) * Ly;
       }
     }
   }

@@ -42,6 +42,9 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   A.fallbacks = c.fallbacks;
   A.u = c.u; A.un = c.un; A.R = c.R; A.out = c.out; A.dt = c.dt;
   A.a = T(c.a); A.b = T(c.b);
+  A.general = c.general ? 1 : 0;
+  A.e = T(c.e); A.c1 = T(c.c1); A.c2 = T(c.c2);
+  A.X1 = c.X1; A.X2 = c.X2;
   return A;
 }
 
@@ -153,6 +156,7 @@ cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T
       return c.stage ? run_sweep_x<T, 3, kStage>(g, A, f, st) : run_sweep_x<T, 3, kWriteL>(g, A, f, st);
     }
     case 4: {
+      // the 2D stage writes the partial stage from the x sweep (same kernel body as kStage)
       const bool f = use_fixed<4>(s);
       return c.stage ? run_sweep_x<T, 4, kStage>(g, A, f, st) : run_sweep_x<T, 4, kWriteL>(g, A, f, st);
     }

@@ -66,7 +66,7 @@ def _grid(lib, **kw):
     return g
 
 
-@pytest.mark.parametrize("bad", [dict(pitch=100), dict(pitch=64), dict(nx=0), dict(ny=2), dict(ndim=3),
+@pytest.mark.parametrize("bad", [dict(pitch=100), dict(pitch=64), dict(nx=0), dict(ny=0), dict(ndim=3),
                                  dict(nvar=2), dict(dtype=5), dict(reserved=1)])
 def test_init_rejects_bad_grid_without_gpu(lib, bad):
     p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
@@ -77,7 +77,8 @@ def test_init_rejects_bad_grid_without_gpu(lib, bad):
 
 def test_init_rejects_bad_params_without_gpu(lib):
     g = _grid(lib)
-    for field, val, code in (("z_p", 3, 1), ("weights", 9, 1), ("eps", 0.0, 1), ("system", 0, 5)):
+    for field, val, code in (("z_p", 3, 1), ("weights", 9, 1), ("eps", 0.0, 1), ("system", 0, 5),
+                             ("integrator", 2, 1), ("reserved", 1, 1)):
         p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
         setattr(p, field, val)
         with pytest.raises(lib.WcnsError) as e:

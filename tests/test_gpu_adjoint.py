@@ -166,3 +166,43 @@ def test_gradient_matches_finite_differences_fp64(W):
             errs.append(abs(ad - fd) / abs(fd))
     S.close()
     assert min(errs) < 1e-6, (ad, errs)
+
+
+def test_adjoint_configuration_gradient_matches_finite_differences(W):
+    """The adjoint workload's setup (isentropic vortex with 1 % density noise, frozen-alpha
+    LLF at the initial maximum wave speed, constant CFL-0.5 dt, FE at xi = 100, p = 2,
+    characteristic projection, eps = 1e-4) at 128^2 and 50 steps: the gradient of the L2
+    density mismatch with respect to the initial density agrees with a fourth-order
+    central difference of the GPU forward to 1e-6 relative."""
+    import torch
+    from paper_2306_09760_gb300 import autograd as wag
+    n, steps = 128, 50
+    P = inputs.vortex(n, seed=0)
+    uu, vv, pp = P.extra["u"], P.extra["v"], P.extra["p"]
+    c = np.sqrt(1.4 * pp / P.extra["rho0"])
+    amax = float(max((np.abs(uu) + c).max(), (np.abs(vv) + c).max()))
+    h = P.h[0]
+    dt = 0.5 * h / amax
+    params = dict(flux="LLF_FROZEN", alpha=(amax, amax), xi=100.0, zp=2, characteristic=True, eps=1e-4)
+    rstar = torch.as_tensor(inputs.vortex_primitive(n, t=steps * dt)[0], device="cuda")
+    U = torch.as_tensor(uu, device="cuda"); V = torch.as_tensor(vv, device="cuda")
+    pr = torch.as_tensor(pp, device="cuda")
+    S = W.Solver(P, "f64", stream=torch.cuda.Stream(), **params)
+
+    def J(rho0):
+        E = pr / 0.4 + 0.5 * rho0 * (U * U + V * V)
+        uT = wag.rollout(torch.stack([rho0, rho0 * U, rho0 * V, E]), S, dt, steps)
+        return 0.5 * h * h * torch.sum((uT[0] - rstar) ** 2)
+
+    rho0 = torch.as_tensor(P.extra["rho0"], device="cuda").clone().requires_grad_(True)
+    (grad,) = torch.autograd.grad(J(rho0), rho0)
+    dirn = torch.as_tensor(np.random.default_rng(4).normal(size=(n, n)), device="cuda")
+    ad = float(torch.sum(grad * dirn))
+    errs = []
+    with torch.no_grad():
+        f = lambda e: float(J(rho0.detach() + e * dirn))
+        for eps in (1e-5, 1e-6, 1e-7):
+            fd = (-f(2 * eps) + 8 * f(eps) - 8 * f(-eps) + f(-2 * eps)) / (12 * eps)
+            errs.append(abs(ad - fd) / abs(fd))
+    S.close()
+    assert min(errs) < 1e-6, (ad, errs)

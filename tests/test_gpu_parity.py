@@ -263,3 +263,16 @@ def test_fixed_dt_and_graph_replay_match_direct(W, stream):
     np.testing.assert_array_equal(ua, ub)
     ur, _, _, _ = oracle.step(P, dt=1e-4, nsteps=6)
     check64(ua, ur, lambda u0: oracle.step(P, u0, dt=1e-4, nsteps=6)[0], P.u0, "shu-osher fixed dt")
+
+
+@pytest.mark.parametrize("make,steps", [(lambda: inputs.advection_sine(200), 200),
+                                         (lambda: inputs.sod(1024), 150),
+                                         (lambda: inputs.riemann2d(130, seed=1, ny=70), 10)],
+                         ids=["advection", "sod", "riemann2d"])
+def test_rk4_eq16_parity(W, stream, make, steps):
+    """The paper's own protocol: classical RK4 in the form of Eq. 16 at CFL 0.3."""
+    P = make()
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=steps, integrator="RK4", cfl=0.3)
+    ur, tr, takenr, _ = oracle.step(P, nsteps=steps, rk4=True, cfl=0.3)
+    assert taken == takenr == steps and abs(t - tr) <= 1e-13 * tr
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=steps, rk4=True, cfl=0.3)[0], P.u0, P.name + " RK4")
