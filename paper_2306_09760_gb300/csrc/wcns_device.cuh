@@ -48,7 +48,10 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
   r.system = s.system; r.weights = s.weights; r.flux = s.flux;
   r.xi_small = (sizeof(T) == 4 && s.xi < 1e4) ? 1 : 0;
   r.characteristic = s.characteristic; r.zp = s.zp; r.renorm = s.renorm;
-  r.gamma = T(s.gamma); r.gm1 = T(s.gamma - 1.0); r.eps = T(s.eps); r.xi = T(s.xi);
+  r.gamma = T(s.gamma); r.gm1 = T(s.gamma - 1.0); r.xi = T(s.xi);
+  // eps = 1e-40 is below the smallest normal float and single-precision kernels flush
+  // subnormals to zero, so it is raised to 2^-126 there (IS + eps then never vanishes).
+  r.eps = (sizeof(T) == 4 && s.eps < 1.1754943508222875e-38) ? T(1.1754943508222875e-38) : T(s.eps);
   r.cv = T(s.cv); r.harten = T(s.harten);
   for (int d = 0; d < 2; ++d) r.speed[d] = T(s.speed[d]);
   for (int j = 0; j < 3; ++j) { r.null0[j] = T(s.null0[j]); r.null2[j] = T(s.null2[j]); }
@@ -81,6 +84,9 @@ template <> struct Num<double> {
   WCNS_HD static double tanh_(double z) { return tanh(z); }
   WCNS_HD static double sqrt_(double x) { return sqrt(x); }
   WCNS_HD static double abs_(double x) { return fabs(x); }
+  WCNS_HD static double div_(double x, double y) { return x / y; }
+  WCNS_HD static double rcp_(double x) { return 1.0 / x; }
+  WCNS_HD static double z_ratio(double tau, double b) { return tau / b; }
 };
 template <> struct Num<float> {
   // 1 - tanh(9.1) = 2.5e-8 < half an ulp of 1 in single precision.
@@ -88,6 +94,21 @@ template <> struct Num<float> {
   WCNS_HD static float tanh_(float z) { return tanhf(z); }
   WCNS_HD static float sqrt_(float x) { return sqrtf(x); }
   WCNS_HD static float abs_(float x) { return fabsf(x); }
+  // Division through the reciprocal unit (error within 2 ulp for |y| in [2^-126, 2^126];
+  // every divisor of the scheme stays in that range for data below ~1e18).
+  WCNS_HD static float div_(float x, float y) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(x, y);
+#else
+    return x / y;
+#endif
+  }
+  WCNS_HD static float rcp_(float x) { return div_(1.0f, x); }
+  // Z ratio tau / (IS + eps) (Eq. 15).  In single precision eps is at least the smallest
+  // normal float, so next to a jump (tau > 4 with IS = 0) the quotient can overflow;
+  // it is capped at 1e18, where the weight of that stencil is already 1 to within
+  // rounding, as in the double-precision evaluation with eps = 1e-40.
+  WCNS_HD static float z_ratio(float tau, float b) { return fminf(div_(tau, b), 1.0e18f); }
 };
 
 // tanh(z) with an exact select where the result rounds to +-1 anyway.
@@ -297,7 +318,7 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
 // Eq. 13: Henrick's mapping of a JS weight with ideal value d.
 template <typename T>
 WCNS_HD T m_map(T w, T d) {
-  return w * (d + d * d - T(3) * d * w + w * w) / (d * d + (T(1) - T(2) * d) * w);
+  return Num<T>::div_(w * (d + d * d - T(3) * d * w + w * w), d * d + (T(1) - T(2) * d) * w);
 }
 
 // Midpoint value at x_{i+1/2} from five values v0..v4 = u_{i-2}..u_{i+2} (left state), or
@@ -324,13 +345,13 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
   if (weights == 0 || weights == 4) {
     // Eq. 11
     T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
-    T a0 = d0 / (b0 * b0), a1 = d1 / (b1 * b1), a2 = d2 / (b2 * b2);
-    const T isa = T(1) / (a0 + a1 + a2);
+    T a0 = Num<T>::div_(d0, b0 * b0), a1 = Num<T>::div_(d1, b1 * b1), a2 = Num<T>::div_(d2, b2 * b2);
+    const T isa = Num<T>::rcp_(a0 + a1 + a2);
     w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
     if (weights == 4) {
       // Eq. 12-13
       T g0 = m_map<T>(w0, d0), g1 = m_map<T>(w1, d1), g2 = m_map<T>(w2, d2);
-      const T isg = T(1) / (g0 + g1 + g2);
+      const T isg = Num<T>::rcp_(g0 + g1 + g2);
       w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;
     }
   } else {
@@ -343,11 +364,11 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
       const T q = tau / (b0 * b1 * b2);
       r0 = q * (b1 * b2); r1 = q * (b0 * b2); r2 = q * (b0 * b1);
     } else {
-      r0 = tau / b0; r1 = tau / b1; r2 = tau / b2;
+      r0 = Num<T>::z_ratio(tau, b0); r1 = Num<T>::z_ratio(tau, b1); r2 = Num<T>::z_ratio(tau, b2);
     }
     if (zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
     T a0 = d0 * (T(1) + r0), a1 = d1 * (T(1) + r1), a2 = d2 * (T(1) + r2);
-    const T isa = T(1) / (a0 + a1 + a2);
+    const T isa = Num<T>::rcp_(a0 + a1 + a2);
     w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
     if (weights >= 2) {
       bool keep = false;
@@ -362,7 +383,7 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
         T g0 = w0, g1 = w1, g2 = w2;
         fe_map_all<T>(g0, g1, g2, s);
         if (renorm) {
-          const T isg = T(1) / (g0 + g1 + g2);
+          const T isg = Num<T>::rcp_(g0 + g1 + g2);
           w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;
         } else {
           w0 = g0; w1 = g1; w2 = g2;
@@ -387,7 +408,7 @@ template <typename T, int NV>
 WCNS_HD EulerState<T, NV> euler_prim(const T (&U)[NV], T gm1) {
   EulerState<T, NV> st;
   st.rho = U[0];
-  T inv = T(1) / U[0];
+  T inv = Num<T>::rcp_(U[0]);
   st.un = U[1] * inv;
   T E;
   if (NV == 4) {
@@ -424,7 +445,7 @@ template <typename T, int NV>
 WCNS_HD RoeAvg<T, NV> roe_avg(const EulerState<T, NV>& a, const EulerState<T, NV>& b, T gm1) {
   RoeAvg<T, NV> r;
   T sa = Num<T>::sqrt_(a.rho), sb = Num<T>::sqrt_(b.rho);
-  T inv = T(1) / (sa + sb);
+  T inv = Num<T>::rcp_(sa + sb);
   r.u = (sa * a.un + sb * b.un) * inv;
   r.v = (NV == 4) ? (sa * a.ut + sb * b.ut) * inv : T(0);
   r.H = (sa * a.H + sb * b.H) * inv;
@@ -444,7 +465,7 @@ template <typename T, int NV>
 WCNS_HD CharBasis<T, NV> char_basis(const RoeAvg<T, NV>& r, T gm1) {
   CharBasis<T, NV> cb;
   cb.u = r.u; cb.v = r.v; cb.H = r.H; cb.c = r.c;
-  cb.ic = T(1) / r.c;
+  cb.ic = Num<T>::rcp_(r.c);
   cb.b = gm1 * cb.ic * cb.ic;
   cb.hq2 = T(0.5) * (r.u * r.u + r.v * r.v);
   return cb;
@@ -493,8 +514,8 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, 
     if (flux == 3) {
       alpha = s.speed[dir];
     } else {
-      T sl = Num<T>::abs_(a.un) + Num<T>::sqrt_(g * a.p / a.rho);
-      T sr = Num<T>::abs_(b.un) + Num<T>::sqrt_(g * b.p / b.rho);
+      T sl = Num<T>::abs_(a.un) + Num<T>::sqrt_(Num<T>::div_(g * a.p, a.rho));
+      T sr = Num<T>::abs_(b.un) + Num<T>::sqrt_(Num<T>::div_(g * b.p, b.rho));
       alpha = sl >= sr ? sl : sr;
     }
 #pragma unroll
@@ -511,8 +532,8 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, 
     char_project<T, NV>(cb, dU, dW);
     T delta = s.harten * (Num<T>::abs_(r.u) + r.c);
     T l0 = Num<T>::abs_(r.u - r.c), lm = Num<T>::abs_(r.u), l3 = Num<T>::abs_(r.u + r.c);
-    if (l0 < delta) l0 = ((r.u - r.c) * (r.u - r.c) + delta * delta) / (T(2) * delta);
-    if (l3 < delta) l3 = ((r.u + r.c) * (r.u + r.c) + delta * delta) / (T(2) * delta);
+    if (l0 < delta) l0 = Num<T>::div_((r.u - r.c) * (r.u - r.c) + delta * delta, T(2) * delta);
+    if (l3 < delta) l3 = Num<T>::div_((r.u + r.c) * (r.u + r.c) + delta * delta, T(2) * delta);
     dW[0] = l0 * dW[0];
     dW[1] = lm * dW[1];
     if (NV == 4) dW[2] = lm * dW[2];
@@ -524,7 +545,7 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, 
     return;
   }
   // HLLC with Einfeldt speed estimates
-  T cl = Num<T>::sqrt_(g * a.p / a.rho), cr = Num<T>::sqrt_(g * b.p / b.rho);
+  T cl = Num<T>::sqrt_(Num<T>::div_(g * a.p, a.rho)), cr = Num<T>::sqrt_(Num<T>::div_(g * b.p, b.rho));
   T SL = a.un - cl, SR = b.un + cr;
   if (r.u - r.c < SL) SL = r.u - r.c;
   if (r.u + r.c > SR) SR = r.u + r.c;
@@ -539,13 +560,13 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, 
     return;
   }
   T ml = a.rho * (SL - a.un), mr = b.rho * (SR - b.un);
-  T Sst = (b.p - a.p + a.un * ml - b.un * mr) / (ml - mr);
+  T Sst = Num<T>::div_(b.p - a.p + a.un * ml - b.un * mr, ml - mr);
   const bool left = Sst >= T(0);
   const EulerState<T, NV>& st = left ? a : b;
   T SK = left ? SL : SR;
-  T fac = st.rho * (SK - st.un) / (SK - Sst);
+  T fac = Num<T>::div_(st.rho * (SK - st.un), SK - Sst);
   T EK = left ? UL[NV - 1] : UR[NV - 1];
-  T Est = fac * (EK / st.rho + (Sst - st.un) * (Sst + st.p / (st.rho * (SK - st.un))));
+  T Est = fac * (Num<T>::div_(EK, st.rho) + (Sst - st.un) * (Sst + Num<T>::div_(st.p, st.rho * (SK - st.un))));
   T Us[NV];
   Us[0] = fac;
   Us[1] = fac * Sst;
@@ -562,7 +583,7 @@ WCNS_HD void riemann(const T (&UL)[NV], const T (&UR)[NV], const SchemeT<T>& s, 
 template <typename T, int NV>
 WCNS_HD bool physical(const T (&U)[NV], T gm1) {
   if (!(U[0] > T(0))) return false;
-  T inv = T(1) / U[0];
+  T inv = Num<T>::rcp_(U[0]);
   T kin = (NV == 4) ? (U[1] * U[1] + U[2] * U[2]) * inv : U[1] * U[1] * inv;
   T p = gm1 * (U[NV - 1] - T(0.5) * kin);
   return p > T(0);

@@ -60,16 +60,23 @@ constexpr int kXCells = kXThreads + 5;     // staged cells per block
 template <typename T, int NV>
 constexpr size_t sweep_x_smem() { return sizeof(T) * NV * (kXCells + kXThreads); }
 
+// Single-precision sweeps ask for four resident blocks (32 warps per SM, at most 64
+// registers per thread); double precision keeps the compiler's choice.
+template <typename T>
+constexpr int sweep_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
+
 template <typename T, int NV, int MODE, int FIX>
-__global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
+__global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
   T* sf = su + NV * kXCells;                // [NV][kXThreads]
-  T dt = T(0);
-  if (A.dt) {
-    double d = *A.dt;
-    if (d == 0.0) return;  // the run has reached t_end: the step changes nothing
-    dt = T(d);
+  __shared__ T s_dt;
+  __shared__ int s_skip;
+  // one thread reads the device step (the double-precision pipe is narrow)
+  if (A.dt && threadIdx.x == 0) {
+    const double d = *A.dt;
+    s_skip = (d == 0.0);
+    s_dt = T(d);
   }
   const int64_t row = blockIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * kXTile;
@@ -88,6 +95,11 @@ __global__ void __launch_bounds__(kXThreads) sweep_x_kernel(SweepArgs<T> A) {
     if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
   }
   __syncthreads();
+  T dt = T(0);
+  if (A.dt) {
+    if (s_skip) return;  // the run has reached t_end: the step changes nothing
+    dt = s_dt;
+  }
   const int t = threadIdx.x;
   bool fb = false;
   if (t < ntile + 5) {
@@ -147,15 +159,16 @@ template <typename T, int NV>
 constexpr size_t sweep_y_smem() { return sizeof(T) * NV * (kYCells + kYIfc) * kYCols; }
 
 template <typename T, int NV, int MODE, int FIX>
-__global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> A) {
+__global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep_y_kernel(SweepArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kYCells][kYCols]
   T* sf = su + NV * kYCells * kYCols;       // [NV][kYIfc][kYCols]
-  T dt = T(0);
-  if (A.dt) {
-    double d = *A.dt;
-    if (d == 0.0) return;
-    dt = T(d);
+  __shared__ T s_dt;
+  __shared__ int s_skip;
+  if (A.dt && threadIdx.x == 0 && threadIdx.y == 0) {
+    const double d = *A.dt;
+    s_skip = (d == 0.0);
+    s_dt = T(d);
   }
   const int64_t c0 = (int64_t)blockIdx.x * kYCols;
   const int64_t r0 = (int64_t)blockIdx.y * kYTile;
@@ -170,6 +183,11 @@ __global__ void __launch_bounds__(kYCols * kYRowsT) sweep_y_kernel(SweepArgs<T> 
       su[idx] = A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
   }
   __syncthreads();
+  T dt = T(0);
+  if (A.dt) {
+    if (s_skip) return;
+    dt = s_dt;
+  }
   const int tx = threadIdx.x;
   // the sweep's normal ordering swaps the two momentum components
   constexpr int p1 = (NV == 4) ? 2 : 1;
