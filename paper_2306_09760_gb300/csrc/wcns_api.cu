@@ -28,7 +28,7 @@ struct wcns_ctx {
   void* adj2;
   // small device scalars (one allocation)
   void* scal;
-  double* d_dt;
+  StepDt* d_dt;
   double* d_t;
   long long* d_steps;
   int* d_err;
@@ -219,7 +219,8 @@ cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool 
   d.partials = c->d_partials;
   d.max_blocks = kMaxRedBlocks;
   d.counter = c->d_counters;
-  d.dt_out = maxwave_only ? c->d_out : c->d_dt;
+  d.dt_out = c->d_out;
+  d.step = c->d_dt;
   d.t = maxwave_only ? nullptr : c->d_t;
   d.steps = c->d_steps;
   d.err = c->d_err;
@@ -402,7 +403,7 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
     return from_cuda(e);
   }
   char* b = static_cast<char*>(c->scal);
-  c->d_dt = reinterpret_cast<double*>(b + 0);
+  c->d_dt = reinterpret_cast<StepDt*>(b + 48);
   c->d_t = reinterpret_cast<double*>(b + 8);
   c->d_steps = reinterpret_cast<long long*>(b + 16);
   c->d_err = reinterpret_cast<int*>(b + 24);
@@ -506,7 +507,8 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
   if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
   if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
   // stage states of the forward step, recomputed from the checkpoint u_n
-  WCNS_TRY(cudaMemcpyAsync(c->d_dt, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const StepDt step{dt, (float)dt, 0};
+  WCNS_TRY(cudaMemcpyAsync(c->d_dt, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream));
   WCNS_TRY(stage(c, u_n, nullptr, c->u1, 0.0, 1.0));
   WCNS_TRY(stage(c, c->u1, u_n, c->u2, 0.75, 0.25));
   // reverse of u' = 1/3 u + 2/3 (u2 + dt L(u2)), u2 = 3/4 u + 1/4 (u1 + dt L(u1)), u1 = u + dt L(u):

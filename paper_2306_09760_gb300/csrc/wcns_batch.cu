@@ -30,8 +30,8 @@ struct wcns_batch {
   int* d_n;
   double* d_h;
   double* d_invh;
-  double* d_dt;
-  double* d_tune_dt;
+  StepDt* d_dt;       // per problem
+  StepDt* d_tune_dt;
   double* d_t;
   long long* d_steps;
   unsigned int* d_tickets;   // [4]
@@ -110,7 +110,7 @@ cudaError_t build_items(wcns_batch* b, int nt) {
 
 template <typename T, int NT, int FIX>
 cudaError_t stage_launch(wcns_batch* b, const void* u, const void* un, void* out, double a, double c, int ticket,
-                         const double* dt, int bps) {
+                         const StepDt* dt, int bps) {
   BatchStageArgs<T> A{};
   A.u = static_cast<const T*>(u);
   A.un = static_cast<const T*>(un);
@@ -138,7 +138,7 @@ bool batch_fixed(const Scheme& s) {
 
 template <typename T, int FIX>
 cudaError_t stage_fix(wcns_batch* b, int nt, const void* u, const void* un, void* out, double a, double c, int ticket,
-                      const double* dt, int bps) {
+                      const StepDt* dt, int bps) {
   switch (nt) {
     case 128: return stage_launch<T, 128, FIX>(b, u, un, out, a, c, ticket, dt, bps);
     case 256: return stage_launch<T, 256, FIX>(b, u, un, out, a, c, ticket, dt, bps);
@@ -149,13 +149,13 @@ cudaError_t stage_fix(wcns_batch* b, int nt, const void* u, const void* un, void
 
 template <typename T>
 cudaError_t stage_any(wcns_batch* b, int nt, const void* u, const void* un, void* out, double a, double c, int ticket,
-                      const double* dt, int bps) {
+                      const StepDt* dt, int bps) {
   return batch_fixed(b->s) ? stage_fix<T, 1>(b, nt, u, un, out, a, c, ticket, dt, bps)
                            : stage_fix<T, 0>(b, nt, u, un, out, a, c, ticket, dt, bps);
 }
 
 cudaError_t stage(wcns_batch* b, const void* u, const void* un, void* out, double a, double c, int ticket,
-                  const double* dt, int nt, int bps) {
+                  const StepDt* dt, int nt, int bps) {
   return b->dtype == WCNS_F64 ? stage_any<double>(b, nt, u, un, out, a, c, ticket, dt, bps)
                               : stage_any<float>(b, nt, u, un, out, a, c, ticket, dt, bps);
 }
@@ -178,7 +178,7 @@ int max_blocks_per_sm(const wcns_batch* b, int nt) {
   return f ? max_blocks_fix<float, 1>(nt) : max_blocks_fix<float, 0>(nt);
 }
 
-cudaError_t dt_launch(wcns_batch* b, const void* u, double t_end, double* dt_out, int advance) {
+cudaError_t dt_launch(wcns_batch* b, const void* u, double t_end, StepDt* dt_out, int advance) {
   BatchDtArgs A{};
   A.u = u;
   A.off = b->d_off;
@@ -337,8 +337,8 @@ wcns_status wcns_batch_init(const int64_t* offsets, const int64_t* n, int32_t np
   if (e == cudaSuccess) e = cudaMalloc(&b->d_n, sizeof(int) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_h, sizeof(double) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_invh, sizeof(double) * nprob);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_dt, sizeof(double) * nprob);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tune_dt, sizeof(double) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_dt, sizeof(StepDt) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tune_dt, sizeof(StepDt) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_t, sizeof(double) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_steps, sizeof(long long) * nprob);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tickets, 64);

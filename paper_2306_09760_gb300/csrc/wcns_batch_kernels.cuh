@@ -24,7 +24,7 @@ struct BatchStageArgs {
   const int64_t* off;
   const int* n;
   const double* inv_h;
-  const double* dt;  // per problem
+  const StepDt* dt;  // per problem
   const BatchItem* items;
   int nitems;
   unsigned int* ticket;
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
     const int it = s_item;
     if (it >= A.nitems) break;
     const BatchItem item = A.items[it];
-    const double dtd = A.dt[item.prob];
-    if (dtd != 0.0) {
+    const StepDt& step = A.dt[item.prob];
+    if (!step.zero) {
       const int n = A.n[item.prob];
       const int64_t off = A.off[item.prob];
       const int c0 = item.c0;
@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
 #pragma unroll
           for (int k = 0; k < NV; ++k) S[m][k] = su[k][t + m];
         T F[NV];
-        fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+        if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
+        else fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
 #pragma unroll
         for (int k = 0; k < NV; ++k) sf[k][t] = F[k];
         const bool last = (c0 + TILE >= n);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
       count_fallbacks(fb, A.fallbacks);
       __syncthreads();
       if (t < ntile) {
-        const T dt = T(dtd);
+        const T dt = (sizeof(T) == 4) ? T(step.dt32) : T(step.dt);
         const T inv_h = T(A.inv_h[item.prob]);
         const int64_t o = off + c0 + t;
 #pragma unroll
@@ -104,7 +105,7 @@ struct BatchDtArgs {
   const int64_t* off;
   const int* n;
   const double* h;
-  double* dt;
+  StepDt* dt;
   double* t;
   long long* steps;
   int64_t total;
@@ -121,18 +122,21 @@ __global__ void __launch_bounds__(256) batch_dt_kernel(BatchDtArgs A) {
   const int k = blockIdx.x;
   const int n = A.n[k];
   const int64_t off = A.off[k];
-  double mx = 0.0;
+  // the maximum in the state's precision (exact), widened once per thread
+  T mxT = T(0);
   int bad = 0;
+  const T gam = T(A.gamma), gm1 = T(A.gamma - 1.0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const T rho = u[off + i];
     const T m = u[A.total + off + i];
     const T E = u[2 * A.total + off + i];
     const T inv = T(1) / rho;
     const T vel = m * inv;
-    const T p = T(A.gamma - 1.0) * (E - T(0.5) * rho * vel * vel);
+    const T p = gm1 * (E - T(0.5) * rho * vel * vel);
     if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
-    mx = fmax(mx, (double)(Num<T>::abs_(vel) + Num<T>::sqrt_(T(A.gamma) * p * inv)));
+    mxT = fmax(mxT, Num<T>::abs_(vel) + Num<T>::sqrt_(gam * p * inv));
   }
+  double mx = (double)mxT;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   bad = __any_sync(0xffffffffu, bad);
@@ -157,7 +161,9 @@ __global__ void __launch_bounds__(256) batch_dt_kernel(BatchDtArgs A) {
     if (d > rem) d = rem;
     if (!(d > 0.0)) d = 0.0;
   }
-  A.dt[k] = d;
+  A.dt[k].dt = d;
+  A.dt[k].dt32 = (float)d;
+  A.dt[k].zero = (d == 0.0);
   if (A.advance && d > 0.0) {
     A.t[k] = (A.t_end > 0.0 && d == A.t_end - t) ? A.t_end : t + d;
     A.steps[k] += 1;

@@ -32,12 +32,22 @@ struct Scheme {
   double null0[3], null1[4], null2[3];
 };
 
+// The step of the current RK step as the sweeps read it: the double value, its
+// single-precision copy and a flag for dt == 0 (the run has reached t_end), written
+// together by the step kernel so that single-precision sweeps never use the double pipe.
+struct StepDt {
+  double dt;
+  float dt32;
+  int zero;
+};
+
 // The same parameters in the kernel's own precision (no conversions inside kernels).
 template <typename T>
 struct SchemeT {
   int system, weights, flux, characteristic, zp, renorm;
   int xi_small;  // single precision with xi < 1e4: the FE map uses the exponential form of tanh
   T gamma, gm1, eps, xi, cv, harten;
+  T sat_dist;    // |w - null| at and beyond which every FE tanh term is saturated (kSat / xi)
   T speed[2];
   T null0[3], null1[4], null2[3];
 };
@@ -53,6 +63,8 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
   // subnormals to zero, so it is raised to 2^-126 there (IS + eps then never vanishes).
   r.eps = (sizeof(T) == 4 && s.eps < 1.1754943508222875e-38) ? T(1.1754943508222875e-38) : T(s.eps);
   r.cv = T(s.cv); r.harten = T(s.harten);
+  // rounded up so that xi * |w - null| >= kSat holds whenever the distance test passes
+  r.sat_dist = T((sizeof(T) == 4 ? 9.1 : 20.0) / s.xi * (1.0 + 1e-6));
   for (int d = 0; d < 2; ++d) r.speed[d] = T(s.speed[d]);
   for (int j = 0; j < 3; ++j) { r.null0[j] = T(s.null0[j]); r.null2[j] = T(s.null2[j]); }
   for (int j = 0; j < 4; ++j) r.null1[j] = T(s.null1[j]);
@@ -301,7 +313,7 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
                fmin(fmin(Num<T>::abs_(w1 - s.null1[0]), Num<T>::abs_(w1 - s.null1[1])),
                     fmin(Num<T>::abs_(w1 - s.null1[2]), Num<T>::abs_(w1 - s.null1[3]))));
     d = fmin(d, fmin(fmin(Num<T>::abs_(w2 - s.null2[0]), Num<T>::abs_(w2 - s.null2[1])), Num<T>::abs_(w2 - s.null2[2])));
-    sat = s.xi * d >= Num<T>::kSat;
+    sat = d >= s.sat_dist;
   }
   if (!sat) {
     w0 = fe_map_slow<T>(0, w0, s); w1 = fe_map_slow<T>(1, w1, s); w2 = fe_map_slow<T>(2, w2, s);

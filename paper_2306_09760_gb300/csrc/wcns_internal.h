@@ -30,7 +30,7 @@ struct SweepCall {
   const T* un;
   const T* R;
   T* out;
-  const double* dt;
+  const StepDt* dt;
   double a, b;
   bool stage;  // apply the RK stage update (else write L)
   unsigned long long* fallbacks;
@@ -73,6 +73,7 @@ struct DtLaunch {
   int max_blocks;
   unsigned int* counter;
   double* dt_out;
+  StepDt* step;
   double* t;
   long long* steps;
   int* err;

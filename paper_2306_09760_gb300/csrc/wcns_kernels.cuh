@@ -15,6 +15,7 @@
 #pragma once
 
 #include "wcns_device.cuh"
+#include "wcns_pair.cuh"
 
 namespace wcns {
 
@@ -25,7 +26,7 @@ struct SweepArgs {
   const T* un;         // u^n (read only when a != 0)
   const T* R;          // L_x planes (y sweep of a 2D grid)
   T* out;              // destination (L, L_x or the stage state)
-  const double* dt;    // device step (stage modes)
+  const StepDt* dt;    // device step (stage modes)
   T a, b;
   // General stage form (RK4, Eq. 16): out = a*un + b*u + e*dt*L + c1*X1 + c2*X2.
   // When `general` is 0 the TVD-RK3 form a*un + b*(u + dt*L) is used as written.
@@ -70,13 +71,10 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
   T* sf = su + NV * kXCells;                // [NV][kXThreads]
-  __shared__ T s_dt;
-  __shared__ int s_skip;
-  // one thread reads the device step (the double-precision pipe is narrow)
-  if (A.dt && threadIdx.x == 0) {
-    const double d = *A.dt;
-    s_skip = (d == 0.0);
-    s_dt = T(d);
+  T dt = T(0);
+  if (A.dt) {
+    if (A.dt->zero) return;  // the run has reached t_end: the step changes nothing
+    dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
   const int64_t row = blockIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * kXTile;
@@ -95,11 +93,6 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
     if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
   }
   __syncthreads();
-  T dt = T(0);
-  if (A.dt) {
-    if (s_skip) return;  // the run has reached t_end: the step changes nothing
-    dt = s_dt;
-  }
   const int t = threadIdx.x;
   bool fb = false;
   if (t < ntile + 5) {
@@ -109,7 +102,8 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
 #pragma unroll
       for (int k = 0; k < NV; ++k) S[m][k] = su[k * kXCells + t + m];
     T F[NV];
-    fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+    if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
+    else fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
 #pragma unroll
     for (int k = 0; k < NV; ++k) sf[k * kXThreads + t] = F[k];
     // each interface of the line is counted by exactly one tile
@@ -163,12 +157,10 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kYCells][kYCols]
   T* sf = su + NV * kYCells * kYCols;       // [NV][kYIfc][kYCols]
-  __shared__ T s_dt;
-  __shared__ int s_skip;
-  if (A.dt && threadIdx.x == 0 && threadIdx.y == 0) {
-    const double d = *A.dt;
-    s_skip = (d == 0.0);
-    s_dt = T(d);
+  T dt = T(0);
+  if (A.dt) {
+    if (A.dt->zero) return;
+    dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
   const int64_t c0 = (int64_t)blockIdx.x * kYCols;
   const int64_t r0 = (int64_t)blockIdx.y * kYTile;
@@ -183,11 +175,6 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
       su[idx] = A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
   }
   __syncthreads();
-  T dt = T(0);
-  if (A.dt) {
-    if (s_skip) return;
-    dt = s_dt;
-  }
   const int tx = threadIdx.x;
   // the sweep's normal ordering swaps the two momentum components
   constexpr int p1 = (NV == 4) ? 2 : 1;
@@ -206,7 +193,8 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
         }
       }
       T F[NV];
-      fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
+      if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 1, F);
+      else fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const int dst = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
@@ -275,7 +263,8 @@ struct DtArgs {
   double adv_wave[2];    // |a_d| for advection
   double* partials;      // 2 * gridDim.x
   unsigned int* counter;
-  double* dt_out;
+  double* dt_out;        // max-wave query (t == nullptr): the two maxima
+  StepDt* step;          // step mode: the step the sweeps read
   double* t;
   long long* steps;
   int* err;              // bit 0: non-physical state
@@ -286,9 +275,11 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
   __shared__ double smx[kRedThreads / 32], smy[kRedThreads / 32];
   __shared__ int s_last, s_bad;
   const T* u = static_cast<const T*>(A.u);
-  double mx = 0.0, my = 0.0;
+  // maxima in the state's precision (exact: max never rounds), widened once per thread
+  T mxT = T(0), myT = T(0);
   int bad = 0;
   if (NV > 1) {
+    const T g = T(A.gamma), gm1 = T(A.gamma - 1.0);
     const int64_t ncell = A.nx * A.ny;
     // walk the flattened cell index with (row, column) kept incrementally
     const int64_t stride = (int64_t)gridDim.x * kRedThreads;
@@ -307,13 +298,14 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
       const T E = u[(NV - 1) * A.fstride + off];
       const T inv = T(1) / rho;
       const T ux = mu * inv, vy = mv * inv;
-      const T p = T(A.gamma - 1.0) * (E - T(0.5) * rho * (ux * ux + vy * vy));
+      const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
       if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
-      const T cs = Num<T>::sqrt_(T(A.gamma) * p * inv);
-      mx = fmax(mx, (double)(Num<T>::abs_(ux) + cs));
-      my = fmax(my, (double)(Num<T>::abs_(vy) + cs));
+      const T cs = Num<T>::sqrt_(g * p * inv);
+      mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
+      myT = fmax(myT, Num<T>::abs_(vy) + cs);
     }
   }
+  double mx = (double)mxT, my = (double)myT;
   mx = warp_max(mx);
   my = warp_max(my);
   bad = __any_sync(0xffffffffu, bad);
@@ -377,7 +369,9 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
     if (d > rem) d = rem;
     if (!(d > 0.0)) d = 0.0;
   }
-  *A.dt_out = d;
+  A.step->dt = d;
+  A.step->dt32 = (float)d;
+  A.step->zero = (d == 0.0);
   if (d > 0.0) {
     *A.t = (A.t_end > 0.0 && d == A.t_end - t) ? A.t_end : t + d;
     *A.steps += 1;

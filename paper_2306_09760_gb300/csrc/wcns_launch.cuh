@@ -185,7 +185,7 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
   A.gamma = d.gamma; A.cfl = d.cfl; A.hx = g.h[0]; A.hy = g.h[1];
   A.fixed_dt = d.fixed_dt; A.t_end = d.t_end;
   A.adv_wave[0] = d.adv_wave[0]; A.adv_wave[1] = d.adv_wave[1];
-  A.partials = d.partials; A.counter = d.counter; A.dt_out = d.dt_out; A.t = d.t;
+  A.partials = d.partials; A.counter = d.counter; A.dt_out = d.dt_out; A.step = d.step; A.t = d.t;
   A.steps = d.steps; A.err = d.err;
   const int64_t ncell = g.nx * g.ny;
   int blocks = 1;
