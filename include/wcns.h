@@ -173,8 +173,9 @@ wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t wha
 wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void* b, int32_t what,
                                 void* stream, double* out);
 
-/* Adjoint of one TVD-RK3 step of fixed size dt > 0 (the benchmark spec's hand-written
- * adjoint of steps (a)-(e)): given the checkpoint u_n and the cotangent lam_np1 of
+/* Adjoint of one TVD-RK3 step of fixed size dt > 0 (a hand-written reverse sweep of
+ * the whole step: projection, interpolation, flux, flux difference and the three RK3
+ * stages; the paper has no adjoint): given the checkpoint u_n and the cotangent lam_np1 of
  * u_{n+1} = S(u_n), writes lam_n = (dS/du_n)^T lam_np1.  The stage states u1, u2 are
  * recomputed from u_n (they overwrite the context's stage scratch); the reverse
  * sweeps differentiate the interface flux exactly, including the FE map (Eq. 20),

@@ -1,7 +1,7 @@
 // Packed single-precision evaluation of one interface.
 //
 // The left and right states of an interface go through the same arithmetic: Eq. 5-15
-// on two mirrored five-point stencils, the characteristic projection (Sec. 2.2) of
+// on two mirrored five-point stencils, the characteristic projection of
 // mirrored stencil cells, the back-projection of the two interpolated states and their
 // primitive variables.  Each value is therefore held as a pair (left lane, right lane)
 // in one 64-bit register and every add, multiply and fused multiply-add acts on both
@@ -157,7 +157,7 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
 }
 
 // Characteristic projection of a pair of cells with the basis of one interface (the
-// factored left eigenvectors of Sec. 2.2; P and A carry the factor 1/2).
+// factored left eigenvectors at the Roe state; P and A carry the factor 1/2).
 template <int NV>
 __device__ __forceinline__ void project_pair(const CharBasis<float, NV>& cb, const P2 (&U)[NV], P2 (&W)[NV]) {
   const P2 rho = U[0], m = U[1], E = U[NV - 1];
@@ -211,7 +211,7 @@ __device__ __forceinline__ PrimPair<NV> prim_pair(const P2 (&U)[NV], float gm1) 
   return q;
 }
 
-// Roe average of the two states of a pair (Sec. 2.2).
+// Roe average of the two states of a pair (the state of the characteristic basis).
 template <int NV>
 __device__ __forceinline__ RoeAvg<float, NV> roe_pair(const PrimPair<NV>& q, float gm1) {
   float rl, rr;
