@@ -6,7 +6,7 @@ does, and shares no code with it.  See `wcns_oracle.cpp` for the paper passages 
 function follows.
 
 Parity status: every function is pinned by `tests/test_oracle_*.py` against values
-the paper prints (Table 1 control values), closed forms (the linear scheme's Fourier
+the paper prints (Table 1 and Table B.1 control values), closed forms (the linear scheme's Fourier
 symbol, polynomial exactness, Eq. 18 truncation coefficients, the exact Riemann
 solution), invariants (conservation, symmetry) and central finite differences.
 The weight statistics (`weight_hist`) are parity unpinned: the paper's Tables A.1-A.4
@@ -27,6 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle_wcns.so")
 
 WEIGHTS = {"JS": 0, "Z": 1, "FE": 2, "PFE": 3, "M": 4}
 FLUXES = {"LLF": 0, "ROE": 1, "HLLC": 2, "LLF_FROZEN": 3}
+FAMILIES = {"WCNS": 0, "WENO": 1}
 
 
 class OracleCfg(ctypes.Structure):
@@ -44,11 +45,13 @@ class OracleCfg(ctypes.Structure):
         ("cv", ctypes.c_double),
         ("alpha_x", ctypes.c_double), ("alpha_y", ctypes.c_double),
         ("harten", ctypes.c_double),
+        ("family", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
 DEFAULTS = dict(weights="FE", flux="HLLC", characteristic=True, zp=1, renorm=True,
-                eps=1e-40, xi=1e6, kappa=0.5, cv=1e-3, alpha=(0.0, 0.0), harten=0.1, cfl=0.5)
+                eps=1e-40, xi=1e6, kappa=0.5, cv=1e-3, alpha=(0.0, 0.0), harten=0.1, cfl=0.5,
+                family="WCNS")
 
 
 def build(force: bool = False) -> str:
@@ -74,6 +77,9 @@ def lib():
         cp = P(OracleCfg)
         L.oracle_fe_map.restype = ctypes.c_double
         L.oracle_fe_map.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.oracle_fe_map_family.restype = ctypes.c_double
+        L.oracle_fe_map_family.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double]
         L.oracle_fe_map_deriv.restype = ctypes.c_double
         L.oracle_fe_map_deriv.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_m_map.restype = ctypes.c_double
@@ -143,6 +149,7 @@ def make_cfg(problem=None, **params) -> OracleCfg:
     c.eps, c.xi, c.kappa, c.cv = p["eps"], p["xi"], p["kappa"], p["cv"]
     c.alpha_x, c.alpha_y = p["alpha"]
     c.harten = p["harten"]
+    c.family = FAMILIES[p["family"]] if isinstance(p["family"], str) else int(p["family"])
     if "gamma" in params:
         c.gamma = params["gamma"]
     return c
@@ -159,6 +166,11 @@ def max_threads() -> int:
 def fe_map(i: int, w: float, xi: float = 1e6, kappa: float = 0.5) -> float:
     """Eq. 20 (with phi of Eq. 21) for weight index i."""
     return lib().oracle_fe_map(i, w, xi, kappa)
+
+
+def fe_map_weno(i: int, w: float, xi: float = 1e6, kappa: float = 0.5) -> float:
+    """Eq. 20 with the control rows of App. B, Table B.2 (FE-WENO family)."""
+    return lib().oracle_fe_map_family(1, i, w, xi, kappa)
 
 
 def fe_map_deriv(i: int, w: float, xi: float = 1e6, kappa: float = 0.5) -> float:

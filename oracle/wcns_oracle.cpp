@@ -14,6 +14,8 @@
 //   * Eq. 12-13: M weights.   Eq. 14-15: Z weights.
 //   * Eq. 20-21 with Table 2: the FE mapping function (written with phi, as printed).
 //   * App. A: the PFE switch.
+//   * App. B: the FE-WENO family -- fifth-order finite-difference WENO on Lax-Friedrichs
+//     split fluxes with the Table B.2 control rows (family = 1).
 // Readings where the paper is silent (all listed in the design notes):
 //   * the FE weights map the Z weights and are renormalised after mapping;
 //   * the characteristic projection uses Roe-averaged eigenvectors of the Euler flux
@@ -122,6 +124,8 @@ typedef struct {
   double cv;               // PFE switch width (App. A)
   double alpha_x, alpha_y; // frozen LLF dissipation speeds (flux == 3)
   double harten;           // Roe entropy-fix fraction delta = harten * (|u| + c)
+  int32_t family;          // 0 WCNS (Sec. 2-3), 1 finite-difference WENO on split fluxes (App. B)
+  int32_t pad_;
 } oracle_cfg;
 }
 
@@ -145,6 +149,18 @@ const double kPsi[3][5] = {
     {0.0, 10.0 / 16.0, 2.0 / 3.0, 10.0 / 11.0, 1.0},
     {0.0, 5.0 / 16.0, 1.0 / 3.0, 1.0, 0.0},
 };
+// App. B, Table B.2: the same rows for the fifth-order WENO scheme (ideal weights
+// 1/10, 6/10, 3/10; Table B.1 lists the cases these control points come from).
+const double kOmegaCtrlB[3][5] = {
+    {kW, 1.0 / 10.0, 1.0 / 4.0, kW, 0.0},
+    {kW, 6.0 / 10.0, 1.0 / 2.0, 3.0 / 4.0, kW},
+    {kW, 3.0 / 10.0, 1.0 / 2.0, kW, 0.0},
+};
+const double kPsiB[3][5] = {
+    {0.0, 1.0 / 10.0, 1.0 / 7.0, 1.0, 0.0},
+    {0.0, 6.0 / 10.0, 2.0 / 3.0, 6.0 / 7.0, 1.0},
+    {0.0, 3.0 / 10.0, 1.0 / 3.0, 1.0, 0.0},
+};
 // Eq. 21
 inline double phi_ij(int i, int j) {
   if ((i == 0 && j == 3) || (i == 2 && j == 3) || (i == 1 && j == 4)) return -1.0;
@@ -152,13 +168,15 @@ inline double phi_ij(int i, int j) {
 }
 
 template <class R>
-R fe_map(int i, const R& w, double xi, double kappa) {
+R fe_map(int i, const R& w, double xi, double kappa, int family = 0) {
+  const double(*ctrl)[5] = family == 1 ? kOmegaCtrlB : kOmegaCtrl;
+  const double(*psi)[5] = family == 1 ? kPsiB : kPsi;
   R sum = R(0.0);
   for (int j = 1; j <= kJ[i]; ++j) {
-    R wj = std::isnan(kOmegaCtrl[i][j]) ? w : R(kOmegaCtrl[i][j]);
-    R wjm1 = std::isnan(kOmegaCtrl[i][j - 1]) ? w : R(kOmegaCtrl[i][j - 1]);
+    R wj = std::isnan(ctrl[i][j]) ? w : R(ctrl[i][j]);
+    R wjm1 = std::isnan(ctrl[i][j - 1]) ? w : R(ctrl[i][j - 1]);
     double phi = phi_ij(i, j);
-    double null_point = kappa * (kPsi[i][j] + kPsi[i][j - 1]);
+    double null_point = kappa * (psi[i][j] + psi[i][j - 1]);
     R arg = R(xi * phi) * (w - R(null_point));
     sum = sum + R(phi) * ((wj - wjm1) / R(2.0)) * tanh(arg);
   }
@@ -174,6 +192,7 @@ R m_map(const R& w, double d) {
 }
 
 const double kIdeal[3] = {1.0 / 16.0, 10.0 / 16.0, 5.0 / 16.0};  // Sec. 2, ideal weights d_k
+const double kIdealB[3] = {1.0 / 10.0, 6.0 / 10.0, 3.0 / 10.0};  // App. B, fifth-order WENO
 
 struct WeightTrace {  // optional record of the weights used (statistics)
   double wz[3], wfinal[3];
@@ -185,22 +204,37 @@ struct WeightTrace {  // optional record of the weights used (statistics)
 // mirrored cells u_{i+3}, u_{i+2}, u_{i+1}, u_i, u_{i-1} (right state at i+1/2).
 template <class R>
 R weno_midpoint(const R v[5], const oracle_cfg& c, WeightTrace* tr) {
-  // Eq. 5
+  const double* kId = (c.family == 1) ? kIdealB : kIdeal;
   R q[3];
-  q[0] = (R(3.0) * v[0] - R(10.0) * v[1] + R(15.0) * v[2]) / R(8.0);
-  q[1] = (-v[1] + R(6.0) * v[2] + R(3.0) * v[3]) / R(8.0);
-  q[2] = (R(3.0) * v[2] + R(6.0) * v[3] - v[4]) / R(8.0);
-  // Eq. 10 (h f_k and h^2 s_k in grid units; the factors of h cancel in Eq. 9)
   R hf[3], hhs[3];
+  if (c.family == 1) {
+    // App. B: the classical fifth-order WENO reconstruction at x_{i+1/2} from the
+    // values v = f_{i-2..i+2}: third-order candidates on S0, S1, S2 ...
+    q[0] = (R(2.0) * v[0] - R(7.0) * v[1] + R(11.0) * v[2]) / R(6.0);
+    q[1] = (-v[1] + R(5.0) * v[2] + R(2.0) * v[3]) / R(6.0);
+    q[2] = (R(2.0) * v[2] + R(5.0) * v[3] - v[4]) / R(6.0);
+  } else {
+    // Eq. 5
+    q[0] = (R(3.0) * v[0] - R(10.0) * v[1] + R(15.0) * v[2]) / R(8.0);
+    q[1] = (-v[1] + R(6.0) * v[2] + R(3.0) * v[3]) / R(8.0);
+    q[2] = (R(3.0) * v[2] + R(6.0) * v[3] - v[4]) / R(8.0);
+  }
+  // Eq. 10 (h f_k and h^2 s_k in grid units; the factors of h cancel in Eq. 9)
   hf[0] = (v[0] - R(4.0) * v[1] + R(3.0) * v[2]) / R(2.0);
   hhs[0] = v[0] - R(2.0) * v[1] + v[2];
   hf[1] = (v[3] - v[1]) / R(2.0);
   hhs[1] = v[1] - R(2.0) * v[2] + v[3];
   hf[2] = (R(-3.0) * v[2] + R(4.0) * v[3] - v[4]) / R(2.0);
   hhs[2] = v[2] - R(2.0) * v[3] + v[4];
-  // Eq. 9
   R IS[3];
-  for (int k = 0; k < 3; ++k) IS[k] = hf[k] * hf[k] + hhs[k] * hhs[k];
+  if (c.family == 1) {
+    // ... and the Jiang-Shu indicators IS_k = (h f_k)^2 + 13/12 (h^2 s_k)^2, with h f_k
+    // and h^2 s_k the same differences as in Eq. 10
+    for (int k = 0; k < 3; ++k) IS[k] = R(13.0 / 12.0) * hhs[k] * hhs[k] + hf[k] * hf[k];
+  } else {
+    // Eq. 9
+    for (int k = 0; k < 3; ++k) IS[k] = hf[k] * hf[k] + hhs[k] * hhs[k];
+  }
 
   R w[3];
   if (c.weights == 0 || c.weights == 4) {
@@ -208,7 +242,7 @@ R weno_midpoint(const R v[5], const oracle_cfg& c, WeightTrace* tr) {
     R a[3];
     for (int k = 0; k < 3; ++k) {
       R s = IS[k] + R(c.eps);
-      a[k] = R(kIdeal[k]) / (s * s);
+      a[k] = R(kId[k]) / (s * s);
     }
     R sa = a[0] + a[1] + a[2];
     for (int k = 0; k < 3; ++k) w[k] = a[k] / sa;
@@ -219,7 +253,7 @@ R weno_midpoint(const R v[5], const oracle_cfg& c, WeightTrace* tr) {
     if (c.weights == 4) {
       // Eq. 12-13 (M)
       R b[3];
-      for (int k = 0; k < 3; ++k) b[k] = m_map(w[k], kIdeal[k]);
+      for (int k = 0; k < 3; ++k) b[k] = m_map(w[k], kId[k]);
       R sb = b[0] + b[1] + b[2];
       for (int k = 0; k < 3; ++k) w[k] = b[k] / sb;
     }
@@ -231,7 +265,7 @@ R weno_midpoint(const R v[5], const oracle_cfg& c, WeightTrace* tr) {
       R r = tau / (IS[k] + R(c.eps));
       R rp = r;
       for (int e = 1; e < c.zp; ++e) rp = rp * r;
-      a[k] = R(kIdeal[k]) * (R(1.0) + rp);
+      a[k] = R(kId[k]) * (R(1.0) + rp);
     }
     R sa = a[0] + a[1] + a[2];
     for (int k = 0; k < 3; ++k) w[k] = a[k] / sa;
@@ -245,12 +279,12 @@ R weno_midpoint(const R v[5], const oracle_cfg& c, WeightTrace* tr) {
         // App. A: keep the Z weights when all three lie in [d_k - cv, d_k + cv]
         keep = true;
         for (int k = 0; k < 3; ++k)
-          if (!(val(w[k]) >= kIdeal[k] - c.cv && val(w[k]) <= kIdeal[k] + c.cv)) keep = false;
+          if (!(val(w[k]) >= kId[k] - c.cv && val(w[k]) <= kId[k] + c.cv)) keep = false;
       }
       if (!keep) {
         // Eq. 20 applied to each Z weight, then renormalised
         R g[3];
-        for (int k = 0; k < 3; ++k) g[k] = fe_map(k, w[k], c.xi, c.kappa);
+        for (int k = 0; k < 3; ++k) g[k] = fe_map(k, w[k], c.xi, c.kappa, c.family);
         if (c.renorm) {
           R sg = g[0] + g[1] + g[2];
           for (int k = 0; k < 3; ++k) w[k] = g[k] / sg;
@@ -480,6 +514,70 @@ void record_weights(Stats* st, const WeightTrace& tr) {
   st->samples++;
 }
 
+// App. B (FE-WENO family): finite-difference WENO on Lax-Friedrichs split fluxes.
+// f+-_m = (F(U_m) +- alpha U_m) / 2 for the six stencil cells m = i-2..i+3, with one
+// dissipation speed per interface, alpha = max over those cells of |u_n| + c.  With the
+// characteristic option both split fluxes are projected with the left eigenvectors at the
+// Roe state of (U_i, U_{i+1}); f+ is reconstructed from the left-biased stencil
+// (cells i-2..i+2), f- from the mirrored one (cells i+3..i-1), and the flux at i+1/2 is
+// R (f+^ + f-^).
+template <class R, class Side>
+void weno_split_flux(const R U[6][4], const oracle_cfg& c, const Side& side, R* F) {
+  const int nv = c.nvar;
+  R Fm[6][4];
+  R alpha = R(0.0);
+  for (int m = 0; m < 6; ++m) {
+    physical_flux(U[m], nv, c.gamma, Fm[m]);
+    Prim<R> s = primitive(U[m], nv, c.gamma);
+    alpha = rmax(alpha, fabs(s.un) + sqrt(s.c2));
+  }
+  R gp[6][4], gm[6][4];
+  for (int m = 0; m < 6; ++m)
+    for (int v = 0; v < nv; ++v) {
+      gp[m][v] = R(0.5) * (Fm[m][v] + alpha * U[m][v]);
+      gm[m][v] = R(0.5) * (Fm[m][v] - alpha * U[m][v]);
+    }
+  R Rm[4][4], Lm[4][4];
+  if (c.characteristic) {
+    R u, v, H, cc;
+    roe_average(U[2], U[3], nv, c.gamma, u, v, H, cc);
+    eigenvectors(nv, c.gamma, u, v, H, cc, Rm, Lm);
+    R tp[6][4], tm[6][4];
+    for (int m = 0; m < 6; ++m)
+      for (int k = 0; k < nv; ++k) {
+        R ap = R(0.0), am = R(0.0);
+        for (int q = 0; q < nv; ++q) {
+          ap = ap + Lm[k][q] * gp[m][q];
+          am = am + Lm[k][q] * gm[m][q];
+        }
+        tp[m][k] = ap;
+        tm[m][k] = am;
+      }
+    for (int m = 0; m < 6; ++m)
+      for (int k = 0; k < nv; ++k) {
+        gp[m][k] = tp[m][k];
+        gm[m][k] = tm[m][k];
+      }
+  }
+  R Fh[4];
+  for (int k = 0; k < nv; ++k) {
+    R v5[5];
+    for (int s = 0; s < 5; ++s) v5[s] = gp[s][k];
+    R fp = side(v5);
+    for (int s = 0; s < 5; ++s) v5[s] = gm[5 - s][k];
+    Fh[k] = fp + side(v5);
+  }
+  for (int q = 0; q < nv; ++q) {
+    if (c.characteristic) {
+      R acc = R(0.0);
+      for (int k = 0; k < nv; ++k) acc = acc + Rm[q][k] * Fh[k];
+      F[q] = acc;
+    } else {
+      F[q] = Fh[q];
+    }
+  }
+}
+
 // Midpoint flux at interface k+1/2 of a line of n cells.  `cell(m, var)` reads cell m
 // (already ghost-mapped) of the line in the sweep's normal ordering.
 template <class R, class Cell>
@@ -499,6 +597,18 @@ void interface_flux(int64_t k, int64_t n, int bc, const oracle_cfg& c, double al
     int64_t m = ghost_index(k - 2 + s, n, bc);
     for (int v = 0; v < nv; ++v) U[s][v] = cell(m, v);
   }
+  if (c.system == 0 && c.family == 1) {
+    // App. B on u_t + a u_x = 0: f+ = max(a, 0) u from the left-biased stencil,
+    // f- = min(a, 0) u from the mirrored stencil
+    R a = R(alpha_frozen);
+    R ap = R(0.5) * (a + fabs(a)), am = R(0.5) * (a - fabs(a));
+    R v5[5];
+    for (int s = 0; s < 5; ++s) v5[s] = ap * U[s][0];
+    R fp = side(v5);
+    for (int s = 0; s < 5; ++s) v5[s] = am * U[5 - s][0];
+    F[0] = fp + side(v5);
+    return;
+  }
   if (c.system == 0) {
     // scalar advection: upwind state, F = a u
     R v5[5];
@@ -508,6 +618,10 @@ void interface_flux(int64_t k, int64_t n, int bc, const oracle_cfg& c, double al
     R uR = side(v5);
     R a = R(alpha_frozen);  // the advection speed of this direction
     F[0] = (val(a) >= 0.0) ? a * uL : a * uR;
+    return;
+  }
+  if (c.family == 1) {
+    weno_split_flux(U, c, side, F);
     return;
   }
   R UL[4] = {}, UR[4] = {};
@@ -573,6 +687,15 @@ void line_rhs(int64_t n, int bc, double h, const oracle_cfg& c, double alpha, co
   const int nv = c.nvar;
   // interfaces k+1/2 for k = -3..n+1
   std::vector<R> F((size_t)(n + 5) * nv);
+  if (c.family == 1) {
+    // App. B: conservative finite difference -(F_{i+1/2} - F_{i-1/2}) / h
+    for (int64_t k = -1; k <= n - 1; ++k)
+      interface_flux<R>(k, n, bc, c, alpha, cell, &F[(size_t)(k + 3) * nv], st);
+    for (int64_t i = 0; i < n; ++i)
+      for (int v = 0; v < nv; ++v)
+        out(i, perm[v], -((F[(size_t)(i + 3) * nv + v] - F[(size_t)(i + 2) * nv + v]) / R(h)));
+    return;
+  }
   for (int64_t k = -3; k <= n + 1; ++k)
     interface_flux<R>(k, n, bc, c, alpha, cell, &F[(size_t)(k + 3) * nv], st);
   for (int64_t i = 0; i < n; ++i) {
@@ -701,6 +824,11 @@ int oracle_max_threads(void) {
 
 // Eq. 20 evaluated for weight index i at w (pins for Table 1 / Table 2).
 double oracle_fe_map(int i, double w, double xi, double kappa) { return fe_map<double>(i, w, xi, kappa); }
+
+// Eq. 20 with the App. B (Table B.2) control rows when family == 1.
+double oracle_fe_map_family(int family, int i, double w, double xi, double kappa) {
+  return fe_map<double>(i, w, xi, kappa, family);
+}
 
 // Eq. 13 evaluated at w for ideal weight d.
 double oracle_m_map(double w, double d) { return m_map<double>(w, d); }
