@@ -69,6 +69,12 @@ enum { WCNS_REDUCE_SUM = 0, WCNS_REDUCE_L1 = 1, WCNS_REDUCE_LINF = 2, WCNS_REDUC
 /* Time integrator: third-order TVD Runge-Kutta (Shu-Osher form; default) or the
  * classical fourth-order Runge-Kutta the paper uses, in the form printed as Eq. 16. */
 enum { WCNS_RK3 = 0, WCNS_RK4 = 1 };
+/* Scheme family: the WCNS of Sec. 2-3 (midpoint interpolation of the state, a Riemann
+ * solver, the sixth-order difference of Eq. 3), or the fifth-order finite-difference
+ * WENO of App. B (Lax-Friedrichs split fluxes reconstructed with the same Z/FE weights,
+ * the FE map taking the control rows of Table B.2, and the difference
+ * -(F_{i+1/2} - F_{i-1/2}) / h).  `flux` is ignored by the WENO family. */
+enum { WCNS_FAMILY_WCNS = 0, WCNS_FAMILY_WENO = 1 };
 
 /* Grid descriptor (Sec. 2: uniform cells, h = (hi - lo) / n per direction). */
 typedef struct {
@@ -92,7 +98,7 @@ typedef struct {
   int32_t z_p;             /* Z-weight exponent p of Eq. 14, 1 or 2; default 1 */
   int32_t renorm;          /* 1: renormalise the mapped weights (default) */
   int32_t integrator;      /* WCNS_RK3 (default) or WCNS_RK4 (wcns_step only) */
-  int32_t reserved;        /* must be 0 */
+  int32_t family;          /* WCNS_FAMILY_WCNS (default) or WCNS_FAMILY_WENO */
   double adv_speed[2];     /* advection speed per direction (advection only) */
   double gamma;            /* ratio of specific heats; default 1.4 */
   double eps;              /* epsilon of Eq. 11 / Eq. 14; default 1e-40 (F64), 1e-30 (F32) */
@@ -182,7 +188,8 @@ wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void
  * the Z/JS weights (Eq. 11, 14-15), the characteristic projection and the Roe
  * average, and scatter into cells by gathering (no atomics).
  * Supported: WCNS_EULER (ndim 1 or 2), WCNS_FLUX_LLF_FROZEN (a smooth flux), weights
- * JS / Z / FE / PFE, characteristic 0 or 1; otherwise WCNS_ERR_UNSUPPORTED.
+ * JS / Z / FE / PFE, characteristic 0 or 1, WCNS_RK3, WCNS_FAMILY_WCNS; otherwise
+ * WCNS_ERR_UNSUPPORTED.
  * lam_np1 and lam_n may be the same buffer; u_n must not alias either.  The first
  * call allocates two cotangent buffers of the context (nvar*ny*pitch each).
  * Asynchronous. */

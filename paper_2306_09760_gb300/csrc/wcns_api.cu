@@ -70,10 +70,6 @@ wcns_status from_cuda(cudaError_t e) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Table 2 control points psi_{i,j} (j = 0..J_i), independent of the oracle's copy.
-const double kPsiGpu0[4] = {0.0, 1.0 / 16.0, 1.0 / 11.0, 1.0};
-const double kPsiGpu1[5] = {0.0, 10.0 / 16.0, 2.0 / 3.0, 10.0 / 11.0, 1.0};
-const double kPsiGpu2[4] = {0.0, 5.0 / 16.0, 1.0 / 3.0, 1.0};
 
 wcns_status check_params(const wcns_params* p, int dtype, int nvar, int ndim) {
   if (p->system != WCNS_ADVECTION && p->system != WCNS_EULER) return WCNS_ERR_ARG;
@@ -81,7 +77,7 @@ wcns_status check_params(const wcns_params* p, int dtype, int nvar, int ndim) {
   if (p->flux < WCNS_FLUX_LLF || p->flux > WCNS_FLUX_LLF_FROZEN) return WCNS_ERR_ARG;
   if (p->z_p != 1 && p->z_p != 2) return WCNS_ERR_ARG;
   if (p->integrator != WCNS_RK3 && p->integrator != WCNS_RK4) return WCNS_ERR_ARG;
-  if (p->reserved) return WCNS_ERR_ARG;
+  if (p->family != WCNS_FAMILY_WCNS && p->family != WCNS_FAMILY_WENO) return WCNS_ERR_ARG;
   if (!(p->eps > 0.0) || !(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->xi > 0.0)) return WCNS_ERR_ARG;
   if (!(p->kappa > 0.0) || p->cv < 0.0) return WCNS_ERR_ARG;
   // in single precision eps^2 must stay a normal number for the JS and M weights
@@ -109,9 +105,7 @@ Scheme make_scheme(const wcns_params* p) {
   s.harten = p->harten;
   for (int d = 0; d < 2; ++d)
     s.speed[d] = (p->system == WCNS_ADVECTION) ? p->adv_speed[d] : p->alpha[d];
-  for (int j = 1; j <= 3; ++j) s.null0[j - 1] = p->kappa * (kPsiGpu0[j] + kPsiGpu0[j - 1]);
-  for (int j = 1; j <= 4; ++j) s.null1[j - 1] = p->kappa * (kPsiGpu1[j] + kPsiGpu1[j - 1]);
-  for (int j = 1; j <= 3; ++j) s.null2[j - 1] = p->kappa * (kPsiGpu2[j] + kPsiGpu2[j - 1]);
+  fill_family_tables(s, p->family, p->kappa);
   return s;
 }
 
@@ -501,7 +495,7 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
   const wcns_params& p = c->p;
   if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M ||
-      p.integrator != WCNS_RK3)
+      p.integrator != WCNS_RK3 || p.family != WCNS_FAMILY_WCNS)
     return WCNS_ERR_UNSUPPORTED;
   const size_t bytes = c->nelem * c->elem;
   if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));

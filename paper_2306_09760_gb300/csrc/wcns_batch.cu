@@ -65,9 +65,6 @@ wcns_status from_cuda(cudaError_t e) {
     if (e_ != cudaSuccess) return from_cuda(e_); \
   } while (0)
 
-const double kPsiB0[4] = {0.0, 1.0 / 16.0, 1.0 / 11.0, 1.0};
-const double kPsiB1[5] = {0.0, 10.0 / 16.0, 2.0 / 3.0, 10.0 / 11.0, 1.0};
-const double kPsiB2[4] = {0.0, 5.0 / 16.0, 1.0 / 3.0, 1.0};
 
 Scheme batch_scheme(const wcns_params* p) {
   Scheme s{};
@@ -84,9 +81,7 @@ Scheme batch_scheme(const wcns_params* p) {
   s.harten = p->harten;
   s.speed[0] = p->alpha[0];
   s.speed[1] = p->alpha[1];
-  for (int j = 1; j <= 3; ++j) s.null0[j - 1] = p->kappa * (kPsiB0[j] + kPsiB0[j - 1]);
-  for (int j = 1; j <= 4; ++j) s.null1[j - 1] = p->kappa * (kPsiB1[j] + kPsiB1[j - 1]);
-  for (int j = 1; j <= 3; ++j) s.null2[j - 1] = p->kappa * (kPsiB2[j] + kPsiB2[j - 1]);
+  fill_family_tables(s, p->family, p->kappa);
   return s;
 }
 
@@ -133,7 +128,7 @@ cudaError_t stage_launch(wcns_batch* b, const void* u, const void* un, void* out
 }
 
 bool batch_fixed(const Scheme& s) {
-  return s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1;
+  return s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1 && s.family == 0;
 }
 
 template <typename T, int FIX>

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
           const T* f = &sf[k][t];
-          T L = flux_difference<T>(f[0], f[1], f[2], f[3], f[4], f[5], inv_h);
+          T L = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[1], f[2], f[3], f[4], f[5], inv_h);
           T v = A.b * (su[k][t + 5] + dt * L);
           if (A.a != T(0)) v = A.a * A.un[k * A.total + o] + v;
           A.out[k * A.total + o] = v;

@@ -26,10 +26,14 @@ struct Scheme {
   int characteristic;  // project onto characteristic fields (Euler)
   int zp;              // Z exponent p (1 or 2)
   int renorm;          // renormalise mapped weights
+  int family;          // 0 WCNS (midpoint interpolation, Eq. 3); 1 finite-difference WENO (App. B)
   double gamma, eps, xi, cv, harten;
   double speed[2];     // advection speed (advection) or frozen LF alpha (LLF_FROZEN), per direction
-  // Null points kappa*(psi_j + psi_{j-1}) of Eq. 20 for the three weights (Table 2 rows).
+  // Null points kappa*(psi_j + psi_{j-1}) of Eq. 20 for the three weights (Table 2 rows,
+  // or Table B.2 rows for the WENO family).
   double null0[3], null1[4], null2[3];
+  // Ideal weights and the interior control values omega_{i,j} of those rows.
+  double ideal[3], ctrl0[2], ctrl1[3], ctrl2[2];
 };
 
 // The step of the current RK step as the sweeps read it: the double value, its
@@ -44,20 +48,49 @@ struct StepDt {
 // The same parameters in the kernel's own precision (no conversions inside kernels).
 template <typename T>
 struct SchemeT {
-  int system, weights, flux, characteristic, zp, renorm;
+  int system, weights, flux, characteristic, zp, renorm, family;
   int xi_small;  // single precision with xi < 1e4: the FE map uses the exponential form of tanh
   T gamma, gm1, eps, xi, cv, harten;
   T sat_dist;    // |w - null| at and beyond which every FE tanh term is saturated (kSat / xi)
   T speed[2];
   T null0[3], null1[4], null2[3];
+  T ideal[3], ctrl0[2], ctrl1[3], ctrl2[2];
 };
+
+// Control rows of Eq. 20 for a family: Table 2 (WCNS) or Table B.2 (WENO).  Fills the
+// null points kappa (psi_{i,j} + psi_{i,j-1}), the ideal weights and the interior
+// control values.  Host code; independent of the CPU oracle's tables.
+inline void fill_family_tables(Scheme& s, int family, double kappa) {
+  static const double psi_wcns[3][5] = {{0.0, 1.0 / 16.0, 1.0 / 11.0, 1.0, 0.0},
+                                        {0.0, 10.0 / 16.0, 2.0 / 3.0, 10.0 / 11.0, 1.0},
+                                        {0.0, 5.0 / 16.0, 1.0 / 3.0, 1.0, 0.0}};
+  static const double psi_weno[3][5] = {{0.0, 1.0 / 10.0, 1.0 / 7.0, 1.0, 0.0},
+                                        {0.0, 6.0 / 10.0, 2.0 / 3.0, 6.0 / 7.0, 1.0},
+                                        {0.0, 3.0 / 10.0, 1.0 / 3.0, 1.0, 0.0}};
+  const double(*psi)[5] = family == 1 ? psi_weno : psi_wcns;
+  for (int j = 1; j <= 3; ++j) s.null0[j - 1] = kappa * (psi[0][j] + psi[0][j - 1]);
+  for (int j = 1; j <= 4; ++j) s.null1[j - 1] = kappa * (psi[1][j] + psi[1][j - 1]);
+  for (int j = 1; j <= 3; ++j) s.null2[j - 1] = kappa * (psi[2][j] + psi[2][j - 1]);
+  s.family = family;
+  if (family == 1) {
+    s.ideal[0] = 1.0 / 10.0; s.ideal[1] = 6.0 / 10.0; s.ideal[2] = 3.0 / 10.0;
+    s.ctrl0[0] = 1.0 / 10.0; s.ctrl0[1] = 1.0 / 4.0;
+    s.ctrl1[0] = 6.0 / 10.0; s.ctrl1[1] = 1.0 / 2.0; s.ctrl1[2] = 3.0 / 4.0;
+    s.ctrl2[0] = 3.0 / 10.0; s.ctrl2[1] = 1.0 / 2.0;
+  } else {
+    s.ideal[0] = 1.0 / 16.0; s.ideal[1] = 10.0 / 16.0; s.ideal[2] = 5.0 / 16.0;
+    s.ctrl0[0] = 1.0 / 16.0; s.ctrl0[1] = 1.0 / 6.0;
+    s.ctrl1[0] = 10.0 / 16.0; s.ctrl1[1] = 1.0 / 2.0; s.ctrl1[2] = 5.0 / 6.0;
+    s.ctrl2[0] = 5.0 / 16.0; s.ctrl2[1] = 1.0 / 2.0;
+  }
+}
 
 template <typename T>
 inline SchemeT<T> scheme_as(const Scheme& s) {
   SchemeT<T> r;
   r.system = s.system; r.weights = s.weights; r.flux = s.flux;
   r.xi_small = (sizeof(T) == 4 && s.xi < 1e4) ? 1 : 0;
-  r.characteristic = s.characteristic; r.zp = s.zp; r.renorm = s.renorm;
+  r.characteristic = s.characteristic; r.zp = s.zp; r.renorm = s.renorm; r.family = s.family;
   r.gamma = T(s.gamma); r.gm1 = T(s.gamma - 1.0); r.xi = T(s.xi);
   // eps = 1e-40 is below the smallest normal float and single-precision kernels flush
   // subnormals to zero, so it is raised to 2^-126 there (IS + eps then never vanishes).
@@ -68,20 +101,22 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
   for (int d = 0; d < 2; ++d) r.speed[d] = T(s.speed[d]);
   for (int j = 0; j < 3; ++j) { r.null0[j] = T(s.null0[j]); r.null2[j] = T(s.null2[j]); }
   for (int j = 0; j < 4; ++j) r.null1[j] = T(s.null1[j]);
+  for (int k = 0; k < 3; ++k) { r.ideal[k] = T(s.ideal[k]); r.ctrl1[k] = T(s.ctrl1[k]); }
+  for (int k = 0; k < 2; ++k) { r.ctrl0[k] = T(s.ctrl0[k]); r.ctrl2[k] = T(s.ctrl2[k]); }
   return r;
 }
 
 // Compile-time specialisation of the option switches.  FIX = 0: every option read
-// from the scheme at run time.  FIX = 1: FE weights (Z, p = 1, renormalised), HLLC,
-// characteristic projection -- the default configuration, compiled without the
-// other branches.
+// from the scheme at run time.  FIX = 1: WCNS family, FE weights (Z, p = 1,
+// renormalised), HLLC, characteristic projection -- the default configuration,
+// compiled without the other branches.
 template <int FIX> struct Fixed {
   static constexpr bool on = false;
-  static constexpr int weights = 0, flux = 0, characteristic = 0, zp = 1, renorm = 1;
+  static constexpr int weights = 0, flux = 0, characteristic = 0, zp = 1, renorm = 1, family = 0;
 };
 template <> struct Fixed<1> {
   static constexpr bool on = true;
-  static constexpr int weights = 2, flux = 2, characteristic = 1, zp = 1, renorm = 1;
+  static constexpr int weights = 2, flux = 2, characteristic = 1, zp = 1, renorm = 1, family = 0;
 };
 #define WCNS_OPT(FIX, s, field) (Fixed<FIX>::on ? Fixed<FIX>::field : (s).field)
 
@@ -146,9 +181,9 @@ WCNS_HD T fe_map_exact(int i, T w, const SchemeT<T>& s) {
     T t1 = tanh_sat<T>(xi * (w - s.null0[0]));
     T t2 = tanh_sat<T>(xi * (w - s.null0[1]));
     T t3 = tanh_sat<T>(xi * (w - s.null0[2]));
-    T acc = ((T(1.0 / 16.0) - w) / T(2)) * t1;
-    acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * t2;
-    acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * t3;
+    T acc = ((s.ctrl0[0] - w) / T(2)) * t1;
+    acc = acc + ((s.ctrl0[1] - s.ctrl0[0]) / T(2)) * t2;
+    acc = acc + ((w - s.ctrl0[1]) / T(2)) * t3;
     return acc + w;
   }
   if (i == 1) {
@@ -156,18 +191,18 @@ WCNS_HD T fe_map_exact(int i, T w, const SchemeT<T>& s) {
     T t2 = tanh_sat<T>(xi * (w - s.null1[1]));
     T t3 = tanh_sat<T>(xi * (w - s.null1[2]));
     T t4 = tanh_sat<T>(xi * (w - s.null1[3]));
-    T acc = ((T(10.0 / 16.0) - w) / T(2)) * t1;
-    acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * t2;
-    acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * t3;
-    acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * t4;
+    T acc = ((s.ctrl1[0] - w) / T(2)) * t1;
+    acc = acc + ((s.ctrl1[1] - s.ctrl1[0]) / T(2)) * t2;
+    acc = acc + ((s.ctrl1[2] - s.ctrl1[1]) / T(2)) * t3;
+    acc = acc + ((w - s.ctrl1[2]) / T(2)) * t4;
     return acc + w;
   }
   T t1 = tanh_sat<T>(xi * (w - s.null2[0]));
   T t2 = tanh_sat<T>(xi * (w - s.null2[1]));
   T t3 = tanh_sat<T>(xi * (w - s.null2[2]));
-  T acc = ((T(5.0 / 16.0) - w) / T(2)) * t1;
-  acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * t2;
-  acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * t3;
+  T acc = ((s.ctrl2[0] - w) / T(2)) * t1;
+  acc = acc + ((s.ctrl2[1] - s.ctrl2[0]) / T(2)) * t2;
+  acc = acc + ((w - s.ctrl2[1]) / T(2)) * t3;
   return acc + w;
 }
 
@@ -237,53 +272,56 @@ WCNS_HD T fe_map_expf(T w, const T (&n)[K], const T (&amp)[K + 1], T xi) {
 
 template <typename T>
 WCNS_HD T fe_map0(T w, const SchemeT<T>& s) {
+  const T c0 = s.ctrl0[0], c1 = s.ctrl0[1];
   if constexpr (sizeof(T) == 4) {
     if (s.xi_small) {
-      const T amp[4] = {(T(1.0 / 16.0) - w) / T(2), T(1.0 / 6.0 - 1.0 / 16.0) / T(2), (w - T(1.0 / 6.0)) / T(2), T(0)};
+      const T amp[4] = {(c0 - w) / T(2), (c1 - c0) / T(2), (w - c1) / T(2), T(0)};
       return fe_map_expf<T, 3>(w, s.null0, amp, s.xi) + w;
     }
   }
   if (!all_saturated<T, 3>(w, s.null0, s.xi)) return fe_map_slow<T>(0, w, s);
-  T acc = ((T(1.0 / 16.0) - w) / T(2)) * side_of(w, s.null0[0]);
-  acc = acc + (T(1.0 / 6.0 - 1.0 / 16.0) / T(2)) * side_of(w, s.null0[1]);
-  acc = acc + ((w - T(1.0 / 6.0)) / T(2)) * side_of(w, s.null0[2]);
+  T acc = ((c0 - w) / T(2)) * side_of(w, s.null0[0]);
+  acc = acc + ((c1 - c0) / T(2)) * side_of(w, s.null0[1]);
+  acc = acc + ((w - c1) / T(2)) * side_of(w, s.null0[2]);
   return acc + w;
 }
 template <typename T>
 WCNS_HD T fe_map1(T w, const SchemeT<T>& s) {
+  const T c0 = s.ctrl1[0], c1 = s.ctrl1[1], c2 = s.ctrl1[2];
   if constexpr (sizeof(T) == 4) {
     if (s.xi_small) {
-      const T amp[5] = {(T(10.0 / 16.0) - w) / T(2), T(1.0 / 2.0 - 10.0 / 16.0) / T(2),
-                        T(5.0 / 6.0 - 1.0 / 2.0) / T(2), (w - T(5.0 / 6.0)) / T(2), T(0)};
+      const T amp[5] = {(c0 - w) / T(2), (c1 - c0) / T(2), (c2 - c1) / T(2), (w - c2) / T(2), T(0)};
       return fe_map_expf<T, 4>(w, s.null1, amp, s.xi) + w;
     }
   }
   if (!all_saturated<T, 4>(w, s.null1, s.xi)) return fe_map_slow<T>(1, w, s);
-  T acc = ((T(10.0 / 16.0) - w) / T(2)) * side_of(w, s.null1[0]);
-  acc = acc + (T(1.0 / 2.0 - 10.0 / 16.0) / T(2)) * side_of(w, s.null1[1]);
-  acc = acc + (T(5.0 / 6.0 - 1.0 / 2.0) / T(2)) * side_of(w, s.null1[2]);
-  acc = acc + ((w - T(5.0 / 6.0)) / T(2)) * side_of(w, s.null1[3]);
+  T acc = ((c0 - w) / T(2)) * side_of(w, s.null1[0]);
+  acc = acc + ((c1 - c0) / T(2)) * side_of(w, s.null1[1]);
+  acc = acc + ((c2 - c1) / T(2)) * side_of(w, s.null1[2]);
+  acc = acc + ((w - c2) / T(2)) * side_of(w, s.null1[3]);
   return acc + w;
 }
 template <typename T>
 WCNS_HD T fe_map2(T w, const SchemeT<T>& s) {
+  const T c0 = s.ctrl2[0], c1 = s.ctrl2[1];
   if constexpr (sizeof(T) == 4) {
     if (s.xi_small) {
-      const T amp[4] = {(T(5.0 / 16.0) - w) / T(2), T(1.0 / 2.0 - 5.0 / 16.0) / T(2), (w - T(1.0 / 2.0)) / T(2), T(0)};
+      const T amp[4] = {(c0 - w) / T(2), (c1 - c0) / T(2), (w - c1) / T(2), T(0)};
       return fe_map_expf<T, 3>(w, s.null2, amp, s.xi) + w;
     }
   }
   if (!all_saturated<T, 3>(w, s.null2, s.xi)) return fe_map_slow<T>(2, w, s);
-  T acc = ((T(5.0 / 16.0) - w) / T(2)) * side_of(w, s.null2[0]);
-  acc = acc + (T(1.0 / 2.0 - 5.0 / 16.0) / T(2)) * side_of(w, s.null2[1]);
-  acc = acc + ((w - T(1.0 / 2.0)) / T(2)) * side_of(w, s.null2[2]);
+  T acc = ((c0 - w) / T(2)) * side_of(w, s.null2[0]);
+  acc = acc + ((c1 - c0) / T(2)) * side_of(w, s.null2[1]);
+  acc = acc + ((w - c1) / T(2)) * side_of(w, s.null2[2]);
   return acc + w;
 }
 
 // Eq. 20 for the three weights together.  Where every tanh argument of all three maps
 // is saturated (|xi (w - n)| >= kSat for each null point n), each term is exactly
 // +-amplitude and the sum collapses to a staircase: the identity below the first and
-// above the last null point, the control values of Table 1 in between.  That is
+// above the last null point, the control values of Table 1 (Table B.1 for the WENO
+// family) in between.  That is
 // evaluated by comparisons; otherwise (any argument unsaturated) the exact path runs.
 template <typename T>
 WCNS_HD T null_distance(T w, const T* n, int k) {
@@ -319,11 +357,11 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
     w0 = fe_map_slow<T>(0, w0, s); w1 = fe_map_slow<T>(1, w1, s); w2 = fe_map_slow<T>(2, w2, s);
     return;
   }
-  const T g0 = (w0 < s.null0[1]) ? T(1.0 / 16.0) : T(1.0 / 6.0);
+  const T g0 = (w0 < s.null0[1]) ? s.ctrl0[0] : s.ctrl0[1];
   w0 = (w0 < s.null0[0] || w0 > s.null0[2]) ? w0 : g0;
-  const T g1 = (w1 < s.null1[1]) ? T(10.0 / 16.0) : ((w1 < s.null1[2]) ? T(1.0 / 2.0) : T(5.0 / 6.0));
+  const T g1 = (w1 < s.null1[1]) ? s.ctrl1[0] : ((w1 < s.null1[2]) ? s.ctrl1[1] : s.ctrl1[2]);
   w1 = (w1 < s.null1[0] || w1 > s.null1[3]) ? w1 : g1;
-  const T g2 = (w2 < s.null2[1]) ? T(5.0 / 16.0) : T(1.0 / 2.0);
+  const T g2 = (w2 < s.null2[1]) ? s.ctrl2[0] : s.ctrl2[1];
   w2 = (w2 < s.null2[0] || w2 > s.null2[2]) ? w2 : g2;
 }
 
@@ -340,18 +378,31 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
   const int weights = WCNS_OPT(FIX, s, weights);
   const int zp = WCNS_OPT(FIX, s, zp);
   const int renorm = WCNS_OPT(FIX, s, renorm);
-  const T d0 = T(1.0 / 16.0), d1 = T(10.0 / 16.0), d2 = T(5.0 / 16.0);
-  // Eq. 5 (coefficients divided by 8 beforehand; powers of two, so exactly)
-  T q0 = T(0.375) * v0 - T(1.25) * v1 + T(1.875) * v2;
-  T q1 = -T(0.125) * v1 + T(0.75) * v2 + T(0.375) * v3;
-  T q2 = T(0.375) * v2 + T(0.75) * v3 - T(0.125) * v4;
-  // Eq. 10 scaled by h and h^2, then Eq. 9
+  const int family = WCNS_OPT(FIX, s, family);
+  const T d0 = Fixed<FIX>::on ? T(1.0 / 16.0) : s.ideal[0];
+  const T d1 = Fixed<FIX>::on ? T(10.0 / 16.0) : s.ideal[1];
+  const T d2 = Fixed<FIX>::on ? T(5.0 / 16.0) : s.ideal[2];
+  T q0, q1, q2;
+  if (family == 0) {
+    // Eq. 5 (coefficients divided by 8 beforehand; powers of two, so exactly)
+    q0 = T(0.375) * v0 - T(1.25) * v1 + T(1.875) * v2;
+    q1 = -T(0.125) * v1 + T(0.75) * v2 + T(0.375) * v3;
+    q2 = T(0.375) * v2 + T(0.75) * v3 - T(0.125) * v4;
+  } else {
+    // App. B: the fifth-order WENO candidates at x_{i+1/2}
+    q0 = (T(2) * v0 - T(7) * v1 + T(11) * v2) / T(6);
+    q1 = (-v1 + T(5) * v2 + T(2) * v3) / T(6);
+    q2 = (T(2) * v2 + T(5) * v3 - v4) / T(6);
+  }
+  // Eq. 10 scaled by h and h^2, then Eq. 9 (WENO family: the Jiang-Shu weighting 13/12
+  // of the second-difference term)
   T f0 = (v0 - T(4) * v1 + T(3) * v2) / T(2), s0 = v0 - T(2) * v1 + v2;
   T f1 = (v3 - v1) / T(2), s1 = v1 - T(2) * v2 + v3;
   T f2 = (T(-3) * v2 + T(4) * v3 - v4) / T(2), s2 = v2 - T(2) * v3 + v4;
-  T is0 = f0 * f0 + s0 * s0;
-  T is1 = f1 * f1 + s1 * s1;
-  T is2 = f2 * f2 + s2 * s2;
+  const T cs = (family == 0) ? T(1) : T(13.0 / 12.0);
+  T is0 = f0 * f0 + cs * (s0 * s0);
+  T is1 = f1 * f1 + cs * (s1 * s1);
+  T is2 = f2 * f2 + cs * (s2 * s2);
   const T eps = s.eps;
   T w0, w1, w2;
   if (weights == 0 || weights == 4) {
@@ -601,11 +652,81 @@ WCNS_HD bool physical(const T (&U)[NV], T gm1) {
   return p > T(0);
 }
 
+// App. B (WENO family): the flux at x_{i+1/2} from Lax-Friedrichs split fluxes
+// f+-_m = (F(U_m) +- alpha U_m) / 2 of the six stencil cells, alpha = max over those
+// cells of |u_n| + c (|a| for advection); f+ is reconstructed from cells i-2..i+2,
+// f- from the mirrored cells i+3..i-1, in characteristic fields at the Roe state of
+// (U_i, U_{i+1}) when selected, and the flux is R (f+^ + f-^).
+template <typename T, int NV, int FIX>
+WCNS_HD void weno_split_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV]) {
+  if (NV == 1) {
+    const T a = s.speed[dir];
+    const T ap = T(0.5) * (a + Num<T>::abs_(a)), am = T(0.5) * (a - Num<T>::abs_(a));
+    const T fp = weno_side<T, FIX>(ap * S[0][0], ap * S[1][0], ap * S[2][0], ap * S[3][0], ap * S[4][0], s);
+    const T fm = weno_side<T, FIX>(am * S[5][0], am * S[4][0], am * S[3][0], am * S[2][0], am * S[1][0], s);
+    F[0] = fp + fm;
+    return;
+  }
+  const T gm1 = s.gm1;
+  T gp[6][NV], gmn[6][NV];
+  T alpha = T(0);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const EulerState<T, NV> st = euler_prim<T, NV>(S[m], gm1);
+    T Fm[NV];
+    euler_flux<T, NV>(S[m], st, Fm);
+    const T sp = Num<T>::abs_(st.un) + Num<T>::sqrt_(Num<T>::div_(s.gamma * st.p, st.rho));
+    alpha = sp > alpha ? sp : alpha;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { gp[m][k] = Fm[k]; gmn[m][k] = S[m][k]; }
+  }
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const T f = gp[m][k], u = gmn[m][k];
+      gp[m][k] = T(0.5) * (f + alpha * u);
+      gmn[m][k] = T(0.5) * (f - alpha * u);
+    }
+  T Fh[NV];
+  if (WCNS_OPT(FIX, s, characteristic)) {
+    T Ui[NV], Uj[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { Ui[k] = S[2][k]; Uj[k] = S[3][k]; }
+    const EulerState<T, NV> a = euler_prim<T, NV>(Ui, gm1), b = euler_prim<T, NV>(Uj, gm1);
+    const RoeAvg<T, NV> r = roe_avg<T, NV>(a, b, gm1);
+    const CharBasis<T, NV> cb = char_basis<T, NV>(r, gm1);
+    T Wp[6][NV], Wm[6][NV];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      char_project<T, NV>(cb, gp[m], Wp[m]);
+      char_project<T, NV>(cb, gmn[m], Wm[m]);
+    }
+    T Wh[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      Wh[k] = weno_side<T, FIX>(Wp[0][k], Wp[1][k], Wp[2][k], Wp[3][k], Wp[4][k], s) +
+              weno_side<T, FIX>(Wm[5][k], Wm[4][k], Wm[3][k], Wm[2][k], Wm[1][k], s);
+    char_unproject<T, NV>(cb, Wh, Fh);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      Fh[k] = weno_side<T, FIX>(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], s) +
+              weno_side<T, FIX>(gmn[5][k], gmn[4][k], gmn[3][k], gmn[2][k], gmn[1][k], s);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k] = Fh[k];
+}
+
 // Midpoint flux at one interface from the six stencil states S[0..5] = U_{i-2..i+3}
 // (already in the sweep's normal ordering).  Returns true if the interpolated states
 // were non-physical and the interface fell back to (U_i, U_{i+1}).
 template <typename T, int NV, int FIX>
 WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV]) {
+  if (WCNS_OPT(FIX, s, family) == 1) {
+    weno_split_flux<T, NV, FIX>(S, s, dir, F);
+    return false;
+  }
   if (NV == 1) {
     const T a = s.speed[dir];
     T v;
@@ -660,6 +781,14 @@ WCNS_HD T flux_difference(T f0, T f1, T f2, T f3, T f4, T f5, T inv_h) {
   acc = acc + d2 * (f4 - f1);
   acc = acc + d3 * (f5 - f0);
   return -(acc * inv_h);
+}
+
+// Spatial derivative from the six interface fluxes f[0..5] = F_{i-5/2} .. F_{i+5/2}:
+// Eq. 3 for the WCNS family, -(F_{i+1/2} - F_{i-1/2}) / h for the WENO family (App. B).
+template <typename T>
+WCNS_HD T flux_difference_family(int family, T f0, T f1, T f2, T f3, T f4, T f5, T inv_h) {
+  if (family == 1) return -((f3 - f2) * inv_h);
+  return flux_difference<T>(f0, f1, f2, f3, f4, f5, inv_h);
 }
 
 WCNS_HD int64_t ghost(int64_t i, int64_t n, int bc) {

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const T* f = sf + k * kXThreads + t;
-      T L = flux_difference<T>(f[0], f[1], f[2], f[3], f[4], f[5], A.inv_h);
+      T L = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[1], f[2], f[3], f[4], f[5], A.inv_h);
       if (MODE == kWriteL) {
         A.out[k * A.fstride + off] = L;
       } else {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const T* f = sf + (k * kYIfc + t) * kYCols + tx;
-        T Ly = flux_difference<T>(f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
+        T Ly = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
                                   f[5 * kYCols], A.inv_h);
         // RHS: R = L_x.  Stage: R = a*un + b*(u + dt*L_x) from the x sweep.
         A.out[k * A.fstride + off] =

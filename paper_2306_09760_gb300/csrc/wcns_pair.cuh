@@ -234,6 +234,7 @@ template <int NV, int FIX>
 __device__ __forceinline__ bool interface_flux_pair(const float (&S)[6][NV], const SchemeT<float>& s, int dir,
                                                    float (&F)[NV]) {
   static_assert(NV == 3 || NV == 4, "packed path is for the Euler systems");
+  if (WCNS_OPT(FIX, s, family) == 1) return interface_flux<float, NV, FIX>(S, s, dir, F);  // App. B, scalar
   const float gm1 = s.gm1;
   P2 U[NV];  // (left, right) interpolated states
   if (WCNS_OPT(FIX, s, characteristic)) {

@@ -29,6 +29,7 @@ FLUXES = {"LLF": 0, "ROE": 1, "HLLC": 2, "LLF_FROZEN": 3}
 WCNS_REDUCE_SUM, WCNS_REDUCE_L1, WCNS_REDUCE_LINF, WCNS_REDUCE_MAXWAVE = range(4)
 WCNS_RK3, WCNS_RK4 = 0, 1
 INTEGRATORS = {"RK3": 0, "RK4": 1}
+FAMILIES = {"WCNS": 0, "WENO": 1}
 
 
 class WcnsError(RuntimeError):
@@ -47,7 +48,7 @@ class wcns_grid(ctypes.Structure):
 class wcns_params(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("weights", ctypes.c_int32), ("flux", ctypes.c_int32),
                 ("characteristic", ctypes.c_int32), ("z_p", ctypes.c_int32), ("renorm", ctypes.c_int32),
-                ("integrator", ctypes.c_int32), ("reserved", ctypes.c_int32), ("adv_speed", ctypes.c_double * 2),
+                ("integrator", ctypes.c_int32), ("family", ctypes.c_int32), ("adv_speed", ctypes.c_double * 2),
                 ("gamma", ctypes.c_double),
                 ("eps", ctypes.c_double), ("xi", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("cv", ctypes.c_double), ("cfl", ctypes.c_double), ("alpha", ctypes.c_double * 2),
@@ -274,6 +275,8 @@ def make_params(system: int, dtype: int, **kw) -> wcns_params:
             setattr(p, k, int(bool(v)))
         elif k == "integrator":
             p.integrator = INTEGRATORS[v] if isinstance(v, str) else int(v)
+        elif k == "family":
+            p.family = FAMILIES[v] if isinstance(v, str) else int(v)
         elif k in ("alpha", "adv_speed"):
             arr = getattr(p, k)
             arr[0], arr[1] = float(v[0]), float(v[1])

@@ -78,7 +78,7 @@ def test_init_rejects_bad_grid_without_gpu(lib, bad):
 def test_init_rejects_bad_params_without_gpu(lib):
     g = _grid(lib)
     for field, val, code in (("z_p", 3, 1), ("weights", 9, 1), ("eps", 0.0, 1), ("system", 0, 5),
-                             ("integrator", 2, 1), ("reserved", 1, 1)):
+                             ("integrator", 2, 1), ("family", 2, 1)):
         p = lib.wcns_default_params(lib.WCNS_EULER, lib.WCNS_F64)
         setattr(p, field, val)
         with pytest.raises(lib.WcnsError) as e:
