@@ -370,6 +370,10 @@ def run_variants(args, W, torch, inputs, hbm_peak):
         ("shu_osher_4096_f64", lambda: inputs.shu_osher(4096), "f64", 200, 20, {}),
         ("euler2d_2048_f32_xi100", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f32", 10, 3, dict(xi=100.0)),
         ("advection_200_f64", lambda: inputs.advection_sine(200), "f64", 400, 20, {}),
+        ("euler2d_2048_f32_fe_weno", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f32", 10, 3,
+         dict(family="WENO")),
+        ("euler2d_2048_f64_fe_weno", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f64", 2, 1,
+         dict(family="WENO")),
     ]
     try:
         out["batched_4096_f32"] = run_batched_variant(W, torch, inputs, hbm_peak)

@@ -158,6 +158,21 @@ wcns_status wcns_get_time(wcns_ctx* ctx, double* t, int64_t* steps_taken);
  * Accumulation is FP64 for both element types. */
 wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t what, double* out);
 
+/* Weight statistics of App. A for one evaluation of L(u): counts, over every one-sided
+ * interpolation (both sides of every interface and every field, in both sweeps), the
+ * base weights (the Z weights, or the JS weights before the M map) and the final
+ * weights (FE mapped and renormalised, kept by the PFE switch, or unchanged) in nbins
+ * equal bins of [0, 1], bin = floor(w * nbins + 1e-6) clamped to [0, nbins - 1] (the
+ * ideal weights and control values lie on the edges of 1e4 bins; the offset keeps a
+ * weight that round-off leaves just below an edge in the edge's bin).
+ * Interfaces per line: the n + 5 the Eq. 3 difference reads (WCNS family) or the n + 1
+ * of the two-point difference (WENO family); periodic lines count their wrapped halo
+ * interfaces again.  hist: device array of 6 * nbins uint64_t counters, index
+ * (kind * 3 + k) * nbins + bin with kind 0 = base, 1 = final and k the weight index;
+ * the call adds to it (the caller zeroes it).  1 <= nbins <= 2^20, else WCNS_ERR_ARG.
+ * Asynchronous on the context's stream; u must not be written meanwhile. */
+wcns_status wcns_weight_hist(wcns_ctx* ctx, const void* u, int32_t nbins, uint64_t* hist);
+
 /* The reductions of wcns_reduce (SUM, L1, LINF only) without a context and without
  * any device allocation.  The paper has no counterpart: this serves callers that
  * cannot call cudaMalloc where they need the reduction -- a loop that reserved all of

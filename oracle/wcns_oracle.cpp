@@ -503,11 +503,20 @@ struct Stats {
 
 // Midpoint flux at interface k+1/2 of a line of n cells.  `cell(m, var)` reads cell m
 // (already ghost-mapped) of the line in the sweep's normal ordering.
+// App. A bins [0, 1] into nbins equal subdomains.  The ideal weights and the control
+// values are multiples of 1e-4 and so lie on bin edges; a weight within 1e-10 below an
+// edge (round-off in the renormalisation) is counted in the edge's bin.
+inline int weight_bin(double w, int nbins) {
+  double x = w * nbins + 1e-6;
+  int b = x < 0.0 ? 0 : (int)x;
+  return std::min(nbins - 1, b);
+}
+
 template <class R>
 void record_weights(Stats* st, const WeightTrace& tr) {
   for (int w = 0; w < 3; ++w) {
-    int b0 = std::min(st->nbins - 1, std::max(0, (int)(tr.wz[w] * st->nbins)));
-    int b1 = std::min(st->nbins - 1, std::max(0, (int)(tr.wfinal[w] * st->nbins)));
+    int b0 = weight_bin(tr.wz[w], st->nbins);
+    int b1 = weight_bin(tr.wfinal[w], st->nbins);
     st->hist[(0 * 3 + w) * st->nbins + b0]++;
     st->hist[(1 * 3 + w) * st->nbins + b1]++;
   }

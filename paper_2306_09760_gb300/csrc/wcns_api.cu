@@ -489,6 +489,15 @@ wcns_status wcns_reduce(wcns_ctx* c, const void* a, const void* b, int32_t what,
   return WCNS_OK;
 }
 
+wcns_status wcns_weight_hist(wcns_ctx* c, const void* u, int32_t nbins, uint64_t* hist) {
+  if (!c || !u || !hist || !aligned16(u) || (reinterpret_cast<uintptr_t>(hist) & 7u)) return WCNS_ERR_ARG;
+  if (nbins < 1 || nbins > (1 << 20)) return WCNS_ERR_ARG;
+  unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
+  WCNS_TRY(by_type(c->g.dtype, [&] { return launch_weight_hist<double>(c->gi, c->s, u, nbins, h, c->stream); },
+                   [&] { return launch_weight_hist<float>(c->gi, c->s, u, nbins, h, c->stream); }));
+  return WCNS_OK;
+}
+
 wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const void* lam_np1, void* lam_n) {
   if (!c || !u_n || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(lam_np1) || !aligned16(lam_n))
     return WCNS_ERR_ARG;

@@ -373,8 +373,10 @@ WCNS_HD T m_map(T w, T d) {
 
 // Midpoint value at x_{i+1/2} from five values v0..v4 = u_{i-2}..u_{i+2} (left state), or
 // the mirrored u_{i+3}..u_{i-1} (right state).  Returns the interpolated value.
+// wz, wf (optional): receive the base weights (Z, or JS before the M map) and the final
+// weights, for the weight statistics of App. A.
 template <typename T, int FIX>
-WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
+WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = nullptr, T* wf = nullptr) {
   const int weights = WCNS_OPT(FIX, s, weights);
   const int zp = WCNS_OPT(FIX, s, zp);
   const int renorm = WCNS_OPT(FIX, s, renorm);
@@ -411,6 +413,7 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
     T a0 = Num<T>::div_(d0, b0 * b0), a1 = Num<T>::div_(d1, b1 * b1), a2 = Num<T>::div_(d2, b2 * b2);
     const T isa = Num<T>::rcp_(a0 + a1 + a2);
     w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
+    if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
     if (weights == 4) {
       // Eq. 12-13
       T g0 = m_map<T>(w0, d0), g1 = m_map<T>(w1, d1), g2 = m_map<T>(w2, d2);
@@ -433,6 +436,7 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
     T a0 = d0 * (T(1) + r0), a1 = d1 * (T(1) + r1), a2 = d2 * (T(1) + r2);
     const T isa = Num<T>::rcp_(a0 + a1 + a2);
     w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
+    if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
     if (weights >= 2) {
       bool keep = false;
       if (weights == 3) {
@@ -454,8 +458,41 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
       }
     }
   }
+  if (wf) { wf[0] = w0; wf[1] = w1; wf[2] = w2; }
   // Eq. 6: convex combination
   return w0 * q0 + w1 * q1 + w2 * q2;
+}
+
+// Weight statistics of App. A: histograms [2][3][nbins] (base, final) x (weight index)
+// of every one-sided interpolation, bin = clamp(floor(w * nbins + 1e-6), 0, nbins - 1).
+// The ideal weights and the control values of Tables 1 and B.1 are multiples of 1e-4,
+// so with 1e4 bins they sit exactly on bin edges; the offset (1e-10 in w) puts a
+// weight that round-off leaves just below such an edge into the edge's bin.
+struct WeightRecorder {
+  unsigned long long* hist;
+  int nbins;
+};
+
+template <typename T>
+WCNS_HD int weight_bin(T w, int nbins) {
+  const double x = (double)w * (double)nbins + 1e-6;
+  const int b = x < 0.0 ? 0 : (int)x;
+  return b >= nbins ? nbins - 1 : b;
+}
+
+// weno_side, recording its weights when a recorder is given.
+template <typename T, int FIX>
+WCNS_HD T weno_rec(const WeightRecorder* rec, T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s) {
+  if (!rec) return weno_side<T, FIX>(v0, v1, v2, v3, v4, s);
+  T wz[3], wf[3];
+  const T r = weno_side<T, FIX>(v0, v1, v2, v3, v4, s, wz, wf);
+#ifdef __CUDA_ARCH__
+  for (int k = 0; k < 3; ++k) {
+    atomicAdd(&rec->hist[(0 * 3 + k) * rec->nbins + weight_bin(wz[k], rec->nbins)], 1ull);
+    atomicAdd(&rec->hist[(1 * 3 + k) * rec->nbins + weight_bin(wf[k], rec->nbins)], 1ull);
+  }
+#endif
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -658,12 +695,13 @@ WCNS_HD bool physical(const T (&U)[NV], T gm1) {
 // f- from the mirrored cells i+3..i-1, in characteristic fields at the Roe state of
 // (U_i, U_{i+1}) when selected, and the flux is R (f+^ + f-^).
 template <typename T, int NV, int FIX>
-WCNS_HD void weno_split_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV]) {
+WCNS_HD void weno_split_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV],
+                             const WeightRecorder* rec = nullptr) {
   if (NV == 1) {
     const T a = s.speed[dir];
     const T ap = T(0.5) * (a + Num<T>::abs_(a)), am = T(0.5) * (a - Num<T>::abs_(a));
-    const T fp = weno_side<T, FIX>(ap * S[0][0], ap * S[1][0], ap * S[2][0], ap * S[3][0], ap * S[4][0], s);
-    const T fm = weno_side<T, FIX>(am * S[5][0], am * S[4][0], am * S[3][0], am * S[2][0], am * S[1][0], s);
+    const T fp = weno_rec<T, FIX>(rec, ap * S[0][0], ap * S[1][0], ap * S[2][0], ap * S[3][0], ap * S[4][0], s);
+    const T fm = weno_rec<T, FIX>(rec, am * S[5][0], am * S[4][0], am * S[3][0], am * S[2][0], am * S[1][0], s);
     F[0] = fp + fm;
     return;
   }
@@ -705,14 +743,14 @@ WCNS_HD void weno_split_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, 
     T Wh[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      Wh[k] = weno_side<T, FIX>(Wp[0][k], Wp[1][k], Wp[2][k], Wp[3][k], Wp[4][k], s) +
-              weno_side<T, FIX>(Wm[5][k], Wm[4][k], Wm[3][k], Wm[2][k], Wm[1][k], s);
+      Wh[k] = weno_rec<T, FIX>(rec, Wp[0][k], Wp[1][k], Wp[2][k], Wp[3][k], Wp[4][k], s) +
+              weno_rec<T, FIX>(rec, Wm[5][k], Wm[4][k], Wm[3][k], Wm[2][k], Wm[1][k], s);
     char_unproject<T, NV>(cb, Wh, Fh);
   } else {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      Fh[k] = weno_side<T, FIX>(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], s) +
-              weno_side<T, FIX>(gmn[5][k], gmn[4][k], gmn[3][k], gmn[2][k], gmn[1][k], s);
+      Fh[k] = weno_rec<T, FIX>(rec, gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], s) +
+              weno_rec<T, FIX>(rec, gmn[5][k], gmn[4][k], gmn[3][k], gmn[2][k], gmn[1][k], s);
   }
 #pragma unroll
   for (int k = 0; k < NV; ++k) F[k] = Fh[k];
@@ -722,16 +760,24 @@ WCNS_HD void weno_split_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, 
 // (already in the sweep's normal ordering).  Returns true if the interpolated states
 // were non-physical and the interface fell back to (U_i, U_{i+1}).
 template <typename T, int NV, int FIX>
-WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV]) {
+WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T (&F)[NV],
+                            const WeightRecorder* rec = nullptr) {
   if (WCNS_OPT(FIX, s, family) == 1) {
-    weno_split_flux<T, NV, FIX>(S, s, dir, F);
+    weno_split_flux<T, NV, FIX>(S, s, dir, F, rec);
     return false;
   }
   if (NV == 1) {
     const T a = s.speed[dir];
     T v;
-    if (a >= T(0)) v = weno_side<T, FIX>(S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
-    else v = weno_side<T, FIX>(S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
+    if (rec) {  // statistics count both one-sided interpolations
+      const T vl = weno_rec<T, FIX>(rec, S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
+      const T vr = weno_rec<T, FIX>(rec, S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
+      v = (a >= T(0)) ? vl : vr;
+    } else if (a >= T(0)) {
+      v = weno_side<T, FIX>(S[0][0], S[1][0], S[2][0], S[3][0], S[4][0], s);
+    } else {
+      v = weno_side<T, FIX>(S[5][0], S[4][0], S[3][0], S[2][0], S[1][0], s);
+    }
     F[0] = a * v;
     return false;
   }
@@ -750,16 +796,16 @@ WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T
     T WL[NV], WR[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      WL[k] = weno_side<T, FIX>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
-      WR[k] = weno_side<T, FIX>(W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
+      WL[k] = weno_rec<T, FIX>(rec, W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
+      WR[k] = weno_rec<T, FIX>(rec, W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
     }
     char_unproject<T, NV>(cb, WL, UL);
     char_unproject<T, NV>(cb, WR, UR);
   } else {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      UL[k] = weno_side<T, FIX>(S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
-      UR[k] = weno_side<T, FIX>(S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
+      UL[k] = weno_rec<T, FIX>(rec, S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
+      UR[k] = weno_rec<T, FIX>(rec, S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
     }
   }
   bool fallback = false;

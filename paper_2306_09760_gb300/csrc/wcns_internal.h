@@ -81,6 +81,12 @@ struct DtLaunch {
 template <typename T>
 cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st);
 
+// App. A weight statistics of one evaluation of L(u), accumulated into
+// hist[2][3][nbins] (device, 64-bit counters).
+template <typename T>
+cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u, int nbins,
+                               unsigned long long* hist, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int what, double* partials,
                           int max_blocks, unsigned int* counters, double* out, cudaStream_t st);

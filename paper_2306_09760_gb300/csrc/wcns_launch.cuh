@@ -4,6 +4,7 @@
 #include "wcns_internal.h"
 #include "wcns_kernels.cuh"
 #include "wcns_adjoint_kernels.cuh"
+#include "wcns_stats.cuh"
 
 namespace wcns {
 
@@ -220,6 +221,41 @@ cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int w
 
 }  // namespace wcns
 
+namespace wcns {
+
+template <typename T>
+cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u, int nbins,
+                               unsigned long long* hist, cudaStream_t st) {
+  for (int dir = 0; dir < g.ndim; ++dir) {
+    HistArgs<T> A{};
+    A.u = static_cast<const T*>(u);
+    A.n = dir == 0 ? g.nx : g.ny;
+    A.lines = dir == 0 ? g.ny : g.nx;
+    A.pitch = g.pitch;
+    A.fstride = g.ny * g.pitch;
+    A.dir = dir;
+    A.bc = g.bc[dir];
+    A.kmin = s.family == 1 ? -1 : -3;
+    A.nk = s.family == 1 ? A.n + 1 : A.n + 5;
+    A.s = scheme_as<T>(s);
+    A.rec.hist = hist;
+    A.rec.nbins = nbins;
+    const int64_t threads = A.lines * A.nk;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    switch (g.nvar) {
+      case 1: weight_hist_kernel<T, 1><<<blocks, 256, 0, st>>>(A); break;
+      case 3: weight_hist_kernel<T, 3><<<blocks, 256, 0, st>>>(A); break;
+      case 4: weight_hist_kernel<T, 4><<<blocks, 256, 0, st>>>(A); break;
+      default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace wcns
+
 #define WCNS_INSTANTIATE(T)                                                                          \
   namespace wcns {                                                                                   \
   template cudaError_t configure_kernels<T>(int);                                                    \
@@ -232,6 +268,8 @@ cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int w
   template cudaError_t launch_adjoint_y<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
                                            cudaStream_t);                                            \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
+  template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const void*, int,       \
+                                             unsigned long long*, cudaStream_t);                     \
   template cudaError_t launch_reduce<T>(const GridInfo&, const void*, const void*, int, double*, int, \
                                         unsigned int*, double*, cudaStream_t);                       \
   }

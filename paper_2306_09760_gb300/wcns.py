@@ -79,6 +79,7 @@ def load():
         "wcns_get_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "wcns_reduce": (st, [vp, vp, vp, ctypes.c_int32, P(ctypes.c_double)]),
         "wcns_adjoint_step": (st, [vp, vp, ctypes.c_double, vp, vp]),
+        "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
         "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
         "wcns_status_string": (ctypes.c_char_p, [st]),
@@ -182,6 +183,12 @@ def wcns_reduce_noalloc(grid: wcns_grid, a, b, what: int, out_dev, stream=None):
     """Context-free, allocation-free reduction; `out_dev` is a device buffer of nvar doubles."""
     _check(load().wcns_reduce_noalloc(ctypes.byref(grid), _ptr(a), _ptr(b), int(what), _stream_handle(stream),
                                       _ptr(out_dev)), "wcns_reduce_noalloc")
+
+
+def wcns_weight_hist(ctx, u, nbins: int, hist):
+    """App. A weight statistics of one L(u), added into the device uint64 tensor `hist`
+    (6 * nbins counters, layout [kind][k][bin])."""
+    _check(load().wcns_weight_hist(ctx, _ptr(u), int(nbins), _ptr(hist)), "wcns_weight_hist")
 
 
 def wcns_adjoint_step(ctx, u_n, dt: float, lam_np1, lam_n):

@@ -463,3 +463,22 @@ def test_flop_count_scales_with_cells():
     a = oracle.count_rhs_flops(inputs.sod(64))
     b = oracle.count_rhs_flops(inputs.sod(128))
     assert a > 0 and abs(b / a - 2.0) < 0.1
+
+
+def test_app_a_fe_weights_raise_the_ideal_share():
+    """App. A, Tables A.1 and A.3: over a shock-tube run the FE weights sit in the bin of the
+    ideal weight more often than the Z weights, for each of the three weights (the
+    absolute shares depend on settings the paper does not state, so only the ordering is
+    pinned).  Sod, N = 200, RK4 at CFL 0.3 (Sec. 4), statistics of every step's RHS."""
+    nb = 10000
+    P = inputs.sod(200)
+    H = np.zeros((2, 3, nb), dtype=np.int64)
+    u, t = P.u0.copy(), 0.0
+    while t < 0.2 * (1 - 1e-12):
+        h, _ = oracle.weight_hist(P, u, nbins=nb)
+        H += h
+        u, t, _, _ = oracle.step(P, u, nsteps=1, t_end=0.2, t0=t, cfl=0.3, rk4=True)
+    tot = H[0, 0].sum()
+    for k, d in enumerate((1 / 16, 10 / 16, 5 / 16)):
+        b = int(d * nb)
+        assert H[1, k, b] > 1.3 * H[0, k, b], (k, H[0, k, b] / tot, H[1, k, b] / tot)
