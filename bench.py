@@ -374,6 +374,8 @@ def run_variants(args, W, torch, inputs, hbm_peak):
          dict(family="WENO")),
         ("euler2d_2048_f64_fe_weno", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f64", 2, 1,
          dict(family="WENO")),
+        ("dmr_960x240_f32_fe_weno", lambda: inputs.dmr(960, 240), "f32", 200, 3, dict(family="WENO")),
+        ("dmr_960x240_f64_fe_weno", lambda: inputs.dmr(960, 240), "f64", 20, 2, dict(family="WENO")),
     ]
     try:
         out["batched_4096_f32"] = run_batched_variant(W, torch, inputs, hbm_peak)

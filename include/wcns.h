@@ -109,6 +109,28 @@ typedef struct {
   double harten;           /* Roe entropy-fix width delta = harten * (|u| + c); default 0.1 */
 } wcns_params;
 
+/* Boundary faces (Sec. 4.3) beyond the grid's periodic / transmissive lines, for the
+ * faces x-lo, x-hi, y-lo, y-hi.  Ghost values are taken at the ghost cell's centre
+ * (lo + (i + 1/2) h) and, for the moving shock, at the time of the state the RK stage
+ * reads (t, t + dt, t + dt/2 for TVD-RK3; t, t + dt/2, t + dt/2, t + dt for RK4):
+ *   WCNS_FACE_GRID            the direction's bc (default)
+ *   WCNS_FACE_TRANSMISSIVE    zero-gradient copy of the edge cell (outflow)
+ *   WCNS_FACE_WALL            inviscid wall: mirror cell with the normal momentum reversed
+ *   WCNS_FACE_FIXED           state_a (inflow)
+ *   WCNS_FACE_FIXED_THEN_WALL state_a where x < wall_x, a wall beyond (y faces)
+ *   WCNS_FACE_SHOCK           state_a where x < shock_x0 + (y + shock_speed t) shock_dxdy,
+ *                             state_b beyond (the exact motion of an oblique shock)
+ * States are primitive (rho, u, v, p); v is ignored on 1D grids. */
+enum { WCNS_FACE_GRID = 0, WCNS_FACE_TRANSMISSIVE = 1, WCNS_FACE_WALL = 2, WCNS_FACE_FIXED = 3,
+       WCNS_FACE_FIXED_THEN_WALL = 4, WCNS_FACE_SHOCK = 5 };
+typedef struct {
+  int32_t type[4];
+  int32_t reserved[4];     /* must be 0 */
+  double state_a[4], state_b[4];
+  double wall_x;
+  double shock_x0, shock_dxdy, shock_speed;
+} wcns_faces;
+
 typedef struct wcns_ctx wcns_ctx;
 typedef struct wcns_batch wcns_batch;
 
@@ -172,6 +194,14 @@ wcns_status wcns_reduce(wcns_ctx* ctx, const void* a, const void* b, int32_t wha
  * the call adds to it (the caller zeroes it).  1 <= nbins <= 2^20, else WCNS_ERR_ARG.
  * Asynchronous on the context's stream; u must not be written meanwhile. */
 wcns_status wcns_weight_hist(wcns_ctx* ctx, const void* u, int32_t nbins, uint64_t* hist);
+
+/* Sets the boundary faces of the context's grid (faces NULL: back to the grid's bc).
+ * Faces apply to wcns_rhs, wcns_step, wcns_step_host and wcns_weight_hist, not to the
+ * adjoint (WCNS_ERR_UNSUPPORTED while faces are set).  Errors: WCNS_ERR_ARG for an
+ * unknown type, a face on a periodic direction or a y face of a 1D grid, or a used
+ * state with rho <= 0 or p <= 0; WCNS_ERR_UNSUPPORTED for wall / state faces on scalar
+ * advection.  Captured step graphs are dropped (rebuilt on the next wcns_step). */
+wcns_status wcns_set_faces(wcns_ctx* ctx, const wcns_faces* faces);
 
 /* The reductions of wcns_reduce (SUM, L1, LINF only) without a context and without
  * any device allocation.  The paper has no counterpart: this serves callers that

@@ -46,6 +46,12 @@ class OracleCfg(ctypes.Structure):
         ("alpha_x", ctypes.c_double), ("alpha_y", ctypes.c_double),
         ("harten", ctypes.c_double),
         ("family", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("face", ctypes.c_int32 * 4),
+        ("state_a", ctypes.c_double * 4), ("state_b", ctypes.c_double * 4),
+        ("wall_x", ctypes.c_double), ("shock_x0", ctypes.c_double),
+        ("shock_dxdy", ctypes.c_double), ("shock_speed", ctypes.c_double),
+        ("lo_x", ctypes.c_double), ("lo_y", ctypes.c_double),
+        ("time", ctypes.c_double),
     ]
 
 
@@ -139,6 +145,16 @@ def make_cfg(problem=None, **params) -> OracleCfg:
         c.system = problem.system
         c.ax, c.ay = problem.adv_speed
         c.gamma = problem.gamma
+        c.lo_x, c.lo_y = problem.lo
+        faces = problem.extra.get("faces") if problem.extra else None
+        if faces:
+            for f in range(4):
+                c.face[f] = int(faces["types"][f])
+            for k in range(4):
+                c.state_a[k] = faces.get("state_a", (0.0,) * 4)[k]
+                c.state_b[k] = faces.get("state_b", (0.0,) * 4)[k]
+            c.wall_x = faces.get("wall_x", 0.0)
+            c.shock_x0, c.shock_dxdy, c.shock_speed = faces.get("shock", (0.0, 0.0, 0.0))
     else:
         c.ndim, c.nvar, c.nx, c.ny, c.hx, c.hy = 1, 1, 1, 1, 1.0, 1.0
         c.system, c.gamma = 0, 1.4
@@ -150,6 +166,7 @@ def make_cfg(problem=None, **params) -> OracleCfg:
     c.alpha_x, c.alpha_y = p["alpha"]
     c.harten = p["harten"]
     c.family = FAMILIES[p["family"]] if isinstance(p["family"], str) else int(p["family"])
+    c.time = float(params.get("time", 0.0))
     if "gamma" in params:
         c.gamma = params["gamma"]
     return c

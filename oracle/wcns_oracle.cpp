@@ -126,6 +126,15 @@ typedef struct {
   double harten;           // Roe entropy-fix fraction delta = harten * (|u| + c)
   int32_t family;          // 0 WCNS (Sec. 2-3), 1 finite-difference WENO on split fluxes (App. B)
   int32_t pad_;
+  // Boundary faces x-lo, x-hi, y-lo, y-hi (Sec. 4.3): 0 the direction's bc, 1 transmissive,
+  // 2 inviscid wall, 3 fixed state A, 4 state A for x < wall_x and a wall beyond,
+  // 5 the moving oblique shock: state A for x < shock_x0 + (y + shock_speed t) shock_dxdy,
+  // state B beyond.  States are primitive (rho, u, v, p).
+  int32_t face[4];
+  double state_a[4], state_b[4];
+  double wall_x, shock_x0, shock_dxdy, shock_speed;
+  double lo_x, lo_y;       // domain origin: cell centres lo + (i + 1/2) h
+  double time;             // time of the state L is evaluated on (moving-shock faces)
 } oracle_cfg;
 }
 
@@ -493,6 +502,41 @@ inline int64_t ghost_index(int64_t i, int64_t n, int bc) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// Cell m of a sweep line, component v in the sweep's normal ordering (component 1 is the
+// normal momentum).  Inside [0, n) it is the stored cell; outside, the face rule of
+// that side gives the ghost value: periodic wrap, transmissive copy of the edge cell,
+// an inviscid wall (mirror cell with the normal momentum reversed), or a prescribed
+// state at the ghost cell's centre (Sec. 4.3: inflow, post-shock strip, moving shock).
+template <class R, class Interior>
+R line_cell(const oracle_cfg& c, int dir, int64_t line, int64_t m, int64_t n, int bc, int v,
+            const Interior& interior) {
+  if (m >= 0 && m < n) return interior(m, v);
+  const int side = m < 0 ? 0 : 1;
+  int type = c.face[2 * dir + side];
+  if (type == 0) type = (bc == 0) ? -1 : 1;
+  const double hx = c.hx, hy = c.hy;
+  const double x = dir == 0 ? c.lo_x + (m + 0.5) * hx : c.lo_x + (line + 0.5) * hx;
+  const double y = dir == 0 ? c.lo_y + (line + 0.5) * hy : c.lo_y + (m + 0.5) * hy;
+  if (type == 4) type = (x < c.wall_x) ? 3 : 2;
+  if (type == -1) return interior(ghost_index(m, n, 0), v);
+  if (type == 1) return interior(ghost_index(m, n, 1), v);
+  if (type == 2) {
+    const int64_t mm = m < 0 ? -1 - m : 2 * n - 1 - m;
+    const R val = interior(mm, v);
+    return v == 1 ? -val : val;
+  }
+  const double* st = c.state_a;
+  if (type == 5) st = (x < c.shock_x0 + (y + c.shock_speed * c.time) * c.shock_dxdy) ? c.state_a : c.state_b;
+  // conservative state in the sweep's ordering
+  const double rho = st[0], un = dir == 0 ? st[1] : st[2], ut = dir == 0 ? st[2] : st[1], p = st[3];
+  if (c.nvar == 3) {
+    const double U[3] = {rho, rho * st[1], p / (c.gamma - 1.0) + 0.5 * rho * st[1] * st[1]};
+    return R(U[v]);
+  }
+  const double U[4] = {rho, rho * un, rho * ut, p / (c.gamma - 1.0) + 0.5 * rho * (un * un + ut * ut)};
+  return R(U[v]);
+}
+
 struct Stats {
   long long nonphysical;
   // weight statistics (optional)
@@ -602,10 +646,8 @@ void interface_flux(int64_t k, int64_t n, int bc, const oracle_cfg& c, double al
     return r;
   };
   R U[6][4];
-  for (int s = 0; s < 6; ++s) {
-    int64_t m = ghost_index(k - 2 + s, n, bc);
-    for (int v = 0; v < nv; ++v) U[s][v] = cell(m, v);
-  }
+  for (int s = 0; s < 6; ++s)
+    for (int v = 0; v < nv; ++v) U[s][v] = cell(k - 2 + s, v);
   if (c.system == 0 && c.family == 1) {
     // App. B on u_t + a u_x = 0: f+ = max(a, 0) u from the left-biased stencil,
     // f- = min(a, 0) u from the mirrored stencil
@@ -730,7 +772,8 @@ void rhs(const oracle_cfg& c, const R* u, R* dudt, Stats* st) {
   double ax = (c.system == 0) ? c.ax : c.alpha_x;
 #pragma omp parallel for schedule(dynamic, 1) if (ny > 1)
   for (int64_t j = 0; j < ny; ++j) {
-    auto cell = [&](int64_t m, int v) -> R { return u[(size_t)v * plane + j * nx + m]; };
+    auto stored = [&](int64_t m, int v) -> R { return u[(size_t)v * plane + j * nx + m]; };
+    auto cell = [&](int64_t m, int v) -> R { return line_cell<R>(c, 0, j, m, nx, c.bcx, v, stored); };
     auto out = [&](int64_t i, int v, const R& x) { dudt[(size_t)v * plane + j * nx + i] = dudt[(size_t)v * plane + j * nx + i] + x; };
     line_rhs<R>(nx, c.bcx, c.hx, c, ax, permx, cell, out, st);
   }
@@ -740,7 +783,8 @@ void rhs(const oracle_cfg& c, const R* u, R* dudt, Stats* st) {
     double ay = (c.system == 0) ? c.ay : c.alpha_y;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < nx; ++i) {
-      auto cell = [&](int64_t m, int v) -> R { return u[(size_t)permy[v] * plane + m * nx + i]; };
+      auto stored = [&](int64_t m, int v) -> R { return u[(size_t)permy[v] * plane + m * nx + i]; };
+      auto cell = [&](int64_t m, int v) -> R { return line_cell<R>(c, 1, i, m, ny, c.bcy, v, stored); };
       auto out = [&](int64_t jj, int v, const R& x) { dudt[(size_t)v * plane + jj * nx + i] = dudt[(size_t)v * plane + jj * nx + i] + x; };
       line_rhs<R>(ny, c.bcy, c.hy, c, ay, permy, cell, out, st);
     }
@@ -780,29 +824,36 @@ double cfl_dt(const oracle_cfg& c, const double* u, double cfl) {
 // Third-order TVD Runge-Kutta step (Shu-Osher form):
 //   u1 = u + dt L(u);  u2 = 3/4 u + 1/4 (u1 + dt L(u1));  u' = 1/3 u + 2/3 (u2 + dt L(u2))
 template <class R>
-void rk3_step(const oracle_cfg& c, R* u, double dt, Stats* st) {
+void rk3_step(const oracle_cfg& c0, R* u, double dt, Stats* st) {
+  // stage times t, t + dt, t + dt/2 (c0.time = t) for time-dependent boundary faces
+  oracle_cfg c = c0;
   const int64_t ncell = c.nx * ((c.ndim == 2) ? c.ny : 1) * c.nvar;
   std::vector<R> L((size_t)ncell), u1((size_t)ncell), u2((size_t)ncell);
   rhs<R>(c, u, L.data(), st);
   for (int64_t q = 0; q < ncell; ++q) u1[q] = u[q] + R(dt) * L[q];
+  c.time = c0.time + dt;
   rhs<R>(c, u1.data(), L.data(), st);
   for (int64_t q = 0; q < ncell; ++q)
     u2[q] = R(0.75) * u[q] + R(0.25) * (u1[q] + R(dt) * L[q]);
+  c.time = c0.time + 0.5 * dt;
   rhs<R>(c, u2.data(), L.data(), st);
   for (int64_t q = 0; q < ncell; ++q)
     u[q] = R(1.0 / 3.0) * u[q] + R(2.0 / 3.0) * (u2[q] + R(dt) * L[q]);
 }
 
 // Classical fourth-order Runge-Kutta (Eq. 16, printed in the form used by the paper).
-void rk4_step(const oracle_cfg& c, double* u, double dt, Stats* st) {
+void rk4_step(const oracle_cfg& c0, double* u, double dt, Stats* st) {
+  oracle_cfg c = c0;  // stage times t, t + dt/2, t + dt/2, t + dt
   const int64_t ncell = c.nx * ((c.ndim == 2) ? c.ny : 1) * c.nvar;
   std::vector<double> L((size_t)ncell), u1((size_t)ncell), u2((size_t)ncell), u3((size_t)ncell);
   rhs<double>(c, u, L.data(), st);
   for (int64_t q = 0; q < ncell; ++q) u1[q] = u[q] + 0.5 * dt * L[q];
+  c.time = c0.time + 0.5 * dt;
   rhs<double>(c, u1.data(), L.data(), st);
   for (int64_t q = 0; q < ncell; ++q) u2[q] = u[q] + 0.5 * dt * L[q];
   rhs<double>(c, u2.data(), L.data(), st);
   for (int64_t q = 0; q < ncell; ++q) u3[q] = u[q] + dt * L[q];
+  c.time = c0.time + dt;
   rhs<double>(c, u3.data(), L.data(), st);
   for (int64_t q = 0; q < ncell; ++q)
     u[q] = -u[q] / 3.0 + u1[q] / 3.0 + 2.0 * u2[q] / 3.0 + u3[q] / 3.0 + dt / 6.0 * L[q];
@@ -922,15 +973,22 @@ void oracle_rhs_cells(const oracle_cfg* c, const double* u, int64_t ncells, cons
       const int bc = dir == 0 ? cfg.bcx : cfg.bcy;
       const double h = dir == 0 ? cfg.hx : cfg.hy;
       const double al = (cfg.system == 0) ? (dir == 0 ? cfg.ax : cfg.ay) : (dir == 0 ? cfg.alpha_x : cfg.alpha_y);
-      auto cell = [&](int64_t m, int v) -> double {
+      auto stored = [&](int64_t m, int v) -> double {
         return dir == 0 ? u[(size_t)perm[v] * plane + j * nx + m] : u[(size_t)perm[v] * plane + m * nx + i];
+      };
+      auto cell = [&](int64_t m, int v) -> double {
+        return line_cell<double>(cfg, dir, dir == 0 ? j : i, m, n, bc, v, stored);
       };
       const int64_t pos = dir == 0 ? i : j;
       double F[6][4];
       for (int k = 0; k < 6; ++k) interface_flux<double>(pos - 3 + k, n, bc, cfg, al, cell, F[k], nullptr);
       for (int v = 0; v < nv; ++v) {
         double a = 0.0;
-        for (int m = 1; m <= 3; ++m) a = a + kD[m - 1] * (F[m + 2][v] - F[3 - m][v]);
+        if (cfg.family == 1) {
+          a = F[3][v] - F[2][v];  // App. B: F_{i+1/2} - F_{i-1/2}
+        } else {
+          for (int m = 1; m <= 3; ++m) a = a + kD[m - 1] * (F[m + 2][v] - F[3 - m][v]);
+        }
         acc[perm[v]] += -(a / h);
       }
     }
@@ -954,7 +1012,9 @@ int oracle_step(const oracle_cfg* c, double* u, double dt, int nsteps, double cf
       d = std::min(d, t_end - tt);
       if (!(d > 0)) break;
     }
-    rk3_step<double>(*c, u, d, &st);
+    oracle_cfg cs = *c;
+    cs.time = tt;
+    rk3_step<double>(cs, u, d, &st);
     tt = (t_end > 0 && d == t_end - tt) ? t_end : tt + d;
     ++taken;
   }
@@ -975,7 +1035,9 @@ int oracle_step_rk4(const oracle_cfg* c, double* u, double dt, int nsteps, doubl
       d = std::min(d, t_end - tt);
       if (!(d > 0)) break;
     }
-    rk4_step(*c, u, d, &st);
+    oracle_cfg cs = *c;
+    cs.time = tt;
+    rk4_step(cs, u, d, &st);
     tt = (t_end > 0 && d == t_end - tt) ? t_end : tt + d;
     ++taken;
   }

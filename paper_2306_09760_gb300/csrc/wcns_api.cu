@@ -15,6 +15,7 @@ struct wcns_ctx {
   wcns_params p;
   Scheme s;
   GridInfo gi;
+  Faces<double> faces;   // boundary faces (active == 0: the grid's bc only)
   cudaStream_t stream;
   int device;
   size_t elem;           // element size in bytes
@@ -139,6 +140,7 @@ struct StageCoef {
   double e, c1, c2;
   const void* X1;
   const void* X2;
+  double cstage;  // the state the stage evaluates L on is at t0 + cstage * dt
 };
 
 template <typename T>
@@ -150,6 +152,9 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   x.e = k.e; x.c1 = k.c1; x.c2 = k.c2;
   x.X1 = static_cast<const T*>(k.X1);
   x.X2 = static_cast<const T*>(k.X2);
+  x.faces = &c->faces;
+  x.cstage = k.cstage;
+  x.tnow = c->d_t;
   if (c->g.ndim == 1) {
     x.un = static_cast<const T*>(un);
     x.out = static_cast<T*>(out);
@@ -180,12 +185,15 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   y.e = k.e;
   y.stage = stage_mode;
   y.fallbacks = c->d_fallbacks;
+  y.faces = &c->faces;
+  y.cstage = k.cstage;
+  y.tnow = c->d_t;
   return timed(c, stage_mode ? kProfSweepYStage : kProfSweepYRhs,
                [&] { return launch_sweep_y<T>(c->gi, c->s, y, c->stream); });
 }
 
 cudaError_t rhs_into(wcns_ctx* c, const void* u, void* out) {
-  StageCoef k{0.0, 1.0, false, 0.0, 0.0, 0.0, nullptr, nullptr};
+  StageCoef k{0.0, 1.0, false, 0.0, 0.0, 0.0, nullptr, nullptr, 0.0};
   return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, nullptr, out, false, k); },
                  [&] { return sweeps<float>(c, u, nullptr, out, false, k); });
 }
@@ -195,9 +203,9 @@ cudaError_t stage_coef(wcns_ctx* c, const void* u, const void* un, void* out, co
                  [&] { return sweeps<float>(c, u, un, out, true, k); });
 }
 
-// TVD-RK3 stage out = a*un + b*(u + dt*L(u)).
-cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b) {
-  StageCoef k{a, b, false, 0.0, 0.0, 0.0, nullptr, nullptr};
+// TVD-RK3 stage out = a*un + b*(u + dt*L(u)), u at time t0 + cstage * dt.
+cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b, double cstage) {
+  StageCoef k{a, b, false, 0.0, 0.0, 0.0, nullptr, nullptr, cstage};
   return stage_coef(c, u, un, out, k);
 }
 
@@ -258,18 +266,19 @@ cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) {
   cudaError_t e;
   if ((e = dt_launch(c, u, dt, t_end, false)) != cudaSuccess) return e;
   if (c->p.integrator == WCNS_RK4) {
-    StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr};
+    StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.0};
     if ((e = stage_coef(c, u, u, c->u1, k1)) != cudaSuccess) return e;
-    StageCoef k2{1.0, 0.0, true, 0.5, 0.0, 0.0, nullptr, nullptr};
+    StageCoef k2{1.0, 0.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.5};
     if ((e = stage_coef(c, c->u1, u, c->u2, k2)) != cudaSuccess) return e;
-    StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr};
+    StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr, 0.5};
     if ((e = stage_coef(c, c->u2, u, c->u3, k3)) != cudaSuccess) return e;
-    StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2};
+    StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2, 1.0};
     return stage_coef(c, c->u3, u, u, k4);
   }
-  if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0)) != cudaSuccess) return e;
-  if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25)) != cudaSuccess) return e;
-  return stage(c, c->u2, u, u, 1.0 / 3.0, 2.0 / 3.0);
+  // stage times t, t + dt, t + dt/2
+  if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0, 0.0)) != cudaSuccess) return e;
+  if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25, 1.0)) != cudaSuccess) return e;
+  return stage(c, c->u2, u, u, 1.0 / 3.0, 2.0 / 3.0, 0.5);
 }
 
 void drop_graph(wcns_ctx* c) {
@@ -397,7 +406,7 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
     return from_cuda(e);
   }
   char* b = static_cast<char*>(c->scal);
-  c->d_dt = reinterpret_cast<StepDt*>(b + 48);
+  c->d_dt = reinterpret_cast<StepDt*>(b + 256);
   c->d_t = reinterpret_cast<double*>(b + 8);
   c->d_steps = reinterpret_cast<long long*>(b + 16);
   c->d_err = reinterpret_cast<int*>(b + 24);
@@ -493,8 +502,55 @@ wcns_status wcns_weight_hist(wcns_ctx* c, const void* u, int32_t nbins, uint64_t
   if (!c || !u || !hist || !aligned16(u) || (reinterpret_cast<uintptr_t>(hist) & 7u)) return WCNS_ERR_ARG;
   if (nbins < 1 || nbins > (1 << 20)) return WCNS_ERR_ARG;
   unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
-  WCNS_TRY(by_type(c->g.dtype, [&] { return launch_weight_hist<double>(c->gi, c->s, u, nbins, h, c->stream); },
-                   [&] { return launch_weight_hist<float>(c->gi, c->s, u, nbins, h, c->stream); }));
+  WCNS_TRY(by_type(
+      c->g.dtype, [&] { return launch_weight_hist<double>(c->gi, c->s, c->faces, c->d_t, u, nbins, h, c->stream); },
+      [&] { return launch_weight_hist<float>(c->gi, c->s, c->faces, c->d_t, u, nbins, h, c->stream); }));
+  return WCNS_OK;
+}
+
+wcns_status wcns_set_faces(wcns_ctx* c, const wcns_faces* f) {
+  if (!c) return WCNS_ERR_ARG;
+  Faces<double> r{};
+  if (f) {
+    for (int k = 0; k < 4; ++k)
+      if (f->reserved[k] != 0) return WCNS_ERR_ARG;
+    for (int k = 0; k < 4; ++k) {
+      const int t = f->type[k];
+      if (t < WCNS_FACE_GRID || t > WCNS_FACE_SHOCK) return WCNS_ERR_ARG;
+      if (t == WCNS_FACE_GRID) continue;
+      const int dir = k / 2;
+      if (dir >= c->g.ndim) return WCNS_ERR_ARG;              // no y faces on 1D grids
+      if (c->g.bc[dir] == WCNS_BC_PERIODIC) return WCNS_ERR_ARG;  // periodic lines have no faces
+      if (t >= WCNS_FACE_WALL && c->p.system != WCNS_EULER) return WCNS_ERR_UNSUPPORTED;
+      r.type[k] = t;
+      r.active = 1;
+    }
+    const double* st[2] = {f->state_a, f->state_b};
+    for (int q = 0; q < 2; ++q) {
+      const double rho = st[q][0], u = st[q][1], v = st[q][2], p = st[q][3];
+      double* U = q == 0 ? r.ua : r.ub;
+      if (r.active && c->p.system == WCNS_EULER && !(rho > 0.0 && p > 0.0)) {
+        bool used = false;
+        for (int k = 0; k < 4; ++k)
+          used = used || (q == 0 ? r.type[k] >= WCNS_FACE_FIXED : r.type[k] == WCNS_FACE_SHOCK);
+        if (used) return WCNS_ERR_ARG;
+      }
+      const double E = p / (c->p.gamma - 1.0) + 0.5 * rho * (u * u + (c->g.nvar == 4 ? v * v : 0.0));
+      U[0] = rho;
+      U[1] = rho * u;
+      if (c->g.nvar == 4) { U[2] = rho * v; U[3] = E; } else { U[2] = E; U[3] = 0.0; }
+    }
+    r.wall_x = f->wall_x;
+    r.x0 = f->shock_x0;
+    r.dxdy = f->shock_dxdy;
+    r.speed = f->shock_speed;
+    r.lo_x = c->g.lo[0];
+    r.lo_y = c->g.lo[1];
+    r.hx = c->gi.h[0];
+    r.hy = c->gi.h[1];
+  }
+  c->faces = r;
+  drop_graph(c);  // captured steps hold the old face arguments
   return WCNS_OK;
 }
 
@@ -504,16 +560,16 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
   const wcns_params& p = c->p;
   if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M ||
-      p.integrator != WCNS_RK3 || p.family != WCNS_FAMILY_WCNS)
+      p.integrator != WCNS_RK3 || p.family != WCNS_FAMILY_WCNS || c->faces.active)
     return WCNS_ERR_UNSUPPORTED;
   const size_t bytes = c->nelem * c->elem;
   if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
   if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
   // stage states of the forward step, recomputed from the checkpoint u_n
-  const StepDt step{dt, (float)dt, 0};
+  const StepDt step{dt, 0.0, (float)dt, 0};
   WCNS_TRY(cudaMemcpyAsync(c->d_dt, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream));
-  WCNS_TRY(stage(c, u_n, nullptr, c->u1, 0.0, 1.0));
-  WCNS_TRY(stage(c, c->u1, u_n, c->u2, 0.75, 0.25));
+  WCNS_TRY(stage(c, u_n, nullptr, c->u1, 0.0, 1.0, 0.0));
+  WCNS_TRY(stage(c, c->u1, u_n, c->u2, 0.75, 0.25, 1.0));
   // reverse of u' = 1/3 u + 2/3 (u2 + dt L(u2)), u2 = 3/4 u + 1/4 (u1 + dt L(u1)), u1 = u + dt L(u):
   //   a2 = 2/3 (lam + dt J(u2)^T lam)
   //   a1 = 1/4 (a2 + dt J(u1)^T a2)

@@ -41,8 +41,24 @@ struct Scheme {
 // together by the step kernel so that single-precision sweeps never use the double pipe.
 struct StepDt {
   double dt;
+  double t0;   // time at the start of the step (stage times t0 + c_k dt)
   float dt32;
   int zero;
+};
+
+// Boundary faces x-lo, x-hi, y-lo, y-hi beyond periodic / transmissive lines (Sec. 4.3):
+// 0 the direction's bc, 1 transmissive, 2 inviscid wall (mirror cell, normal momentum
+// reversed), 3 fixed state A, 4 state A for x < wall_x and a wall beyond, 5 the moving
+// oblique shock (state A for x < x0 + (y + speed t) dxdy, state B beyond).  Ghost values
+// are evaluated at the ghost cell's centre.  States: conservative, storage ordering.
+enum FaceType { kFaceGrid = 0, kFaceTransmissive = 1, kFaceWall = 2, kFaceFixed = 3, kFaceFixedThenWall = 4,
+                kFaceShock = 5 };
+template <typename T>
+struct Faces {
+  int active;
+  int type[4];
+  T ua[4], ub[4];
+  double wall_x, x0, dxdy, speed, lo_x, lo_y, hx, hy;
 };
 
 // The same parameters in the kernel's own precision (no conversions inside kernels).
@@ -83,6 +99,16 @@ inline void fill_family_tables(Scheme& s, int family, double kappa) {
     s.ctrl1[0] = 10.0 / 16.0; s.ctrl1[1] = 1.0 / 2.0; s.ctrl1[2] = 5.0 / 6.0;
     s.ctrl2[0] = 5.0 / 16.0; s.ctrl2[1] = 1.0 / 2.0;
   }
+}
+
+template <typename T>
+inline Faces<T> faces_as(const Faces<double>& f) {
+  Faces<T> r;
+  r.active = f.active;
+  for (int k = 0; k < 4; ++k) { r.type[k] = f.type[k]; r.ua[k] = T(f.ua[k]); r.ub[k] = T(f.ub[k]); }
+  r.wall_x = f.wall_x; r.x0 = f.x0; r.dxdy = f.dxdy; r.speed = f.speed;
+  r.lo_x = f.lo_x; r.lo_y = f.lo_y; r.hx = f.hx; r.hy = f.hy;
+  return r;
 }
 
 template <typename T>
@@ -843,6 +869,45 @@ WCNS_HD int64_t ghost(int64_t i, int64_t n, int bc) {
     return r < 0 ? r + n : r;
   }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Double-precision a + b * c rounded in two steps (no contraction), as the positions of
+// ghost cells and of the moving shock are formed.
+WCNS_HD double add_mul_rn(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, __dmul_rn(b, c));
+#else
+  return a + b * c;
+#endif
+}
+
+// Storage component v of cell m (possibly outside [0, n)) of sweep line `line` in
+// direction dir, with the face rules for ghost cells; `time` is the time of the state
+// (moving-shock faces).
+template <typename T>
+WCNS_HD T face_cell(const T* u, int64_t pitch, int64_t fstride, int dir, int64_t line, int64_t m, int64_t n, int bc,
+                    int v, const Faces<T>& f, double time) {
+  const int64_t base = (int64_t)v * fstride;
+  if (!f.active || (m >= 0 && m < n)) {
+    const int64_t mm = ghost(m, n, bc);
+    return dir == 0 ? u[base + line * pitch + mm] : u[base + mm * pitch + line];
+  }
+  int type = f.type[2 * dir + (m < 0 ? 0 : 1)];
+  if (type == kFaceGrid || type == kFaceTransmissive) {
+    const int64_t mm = ghost(m, n, type == kFaceGrid ? bc : 1);
+    return dir == 0 ? u[base + line * pitch + mm] : u[base + mm * pitch + line];
+  }
+  const double x = add_mul_rn(f.lo_x, double(dir == 0 ? m : line) + 0.5, f.hx);
+  const double y = add_mul_rn(f.lo_y, double(dir == 0 ? line : m) + 0.5, f.hy);
+  if (type == kFaceFixedThenWall) type = (x < f.wall_x) ? kFaceFixed : kFaceWall;
+  if (type == kFaceWall) {
+    const int64_t mm = m < 0 ? -1 - m : 2 * n - 1 - m;
+    const T val = dir == 0 ? u[base + line * pitch + mm] : u[base + mm * pitch + line];
+    return (v == 1 + dir) ? -val : val;
+  }
+  if (type == kFaceShock)
+    return (x < add_mul_rn(f.x0, add_mul_rn(y, f.speed, time), f.dxdy)) ? f.ua[v] : f.ub[v];
+  return f.ua[v];
 }
 
 }  // namespace wcns

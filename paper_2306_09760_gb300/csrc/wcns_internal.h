@@ -39,6 +39,9 @@ struct SweepCall {
   double e, c1, c2;
   const T* X1;
   const T* X2;
+  const Faces<double>* faces;  // boundary faces (active == 0: the grid's bc only)
+  double cstage;               // the state read is at t0 + cstage * dt of the step
+  const double* tnow;          // device time (RHS evaluations)
 };
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
@@ -84,8 +87,8 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st);
 // App. A weight statistics of one evaluation of L(u), accumulated into
 // hist[2][3][nbins] (device, 64-bit counters).
 template <typename T>
-cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u, int nbins,
-                               unsigned long long* hist, cudaStream_t st);
+cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<double>& f, const double* tnow,
+                               const void* u, int nbins, unsigned long long* hist, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int what, double* partials,

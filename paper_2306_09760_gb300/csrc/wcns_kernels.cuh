@@ -39,7 +39,17 @@ struct SweepArgs {
   T inv_h;
   SchemeT<T> s;
   unsigned long long* fallbacks;   // interfaces that fell back to first order
+  Faces<T> f;                      // boundary faces beyond periodic / transmissive lines
+  double cstage;                   // stage time t0 + cstage * dt of the state read (faces)
+  const double* tnow;              // device time (faces, RHS without a step)
 };
+
+// Time of the state a sweep reads, for time-dependent boundary faces.
+template <typename T>
+__device__ __forceinline__ double sweep_time(const SweepArgs<T>& A) {
+  if (!A.f.active) return 0.0;
+  return A.dt ? A.dt->t0 + A.cstage * A.dt->dt : *A.tnow;
+}
 
 // kWriteL: out = L (or L_x).  kStage: out = a*un + b*(u + dt*L).  In a 2D stage the x
 // sweep runs in kStage form with L_x and writes the partial stage into R; the y sweep
@@ -88,9 +98,18 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
 #pragma unroll
     for (int k = 0; k < NV; ++k) unv[k] = A.un[k * A.fstride + row * A.pitch + c0 + threadIdx.x];
   }
-  for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
-    const int v = idx / kXCells, s = idx - v * kXCells;
-    if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
+  if (!A.f.active) {
+    for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
+      const int v = idx / kXCells, s = idx - v * kXCells;
+      if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
+    }
+  } else {
+    const double tf = sweep_time(A);
+    for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
+      const int v = idx / kXCells, s = idx - v * kXCells;
+      if (s < ntile + 10)
+        su[idx] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
+    }
   }
   __syncthreads();
   const int t = threadIdx.x;
@@ -170,12 +189,14 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
   const int ntile = (int)min((int64_t)kYTile, A.ny - r0);
   const int ncol = (int)min((int64_t)kYCols, A.nx - c0);
   const int tid = threadIdx.y * kYCols + threadIdx.x;
+  const double tf = sweep_time(A);
   for (int idx = tid; idx < NV * kYCells * kYCols; idx += kYCols * kYRowsT) {
     const int x = idx % kYCols;
     const int rest = idx / kYCols;
     const int s = rest % kYCells, v = rest / kYCells;
     if (x < ncol && s < ntile + 10)
-      su[idx] = A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
+      su[idx] = A.f.active ? face_cell<T>(A.u, A.pitch, A.fstride, 1, c0 + x, r0 - 5 + s, A.ny, A.bc, v, A.f, tf)
+                           : A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
   }
   __syncthreads();
   const int tx = threadIdx.x;
@@ -373,6 +394,7 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
     if (!(d > 0.0)) d = 0.0;
   }
   A.step->dt = d;
+  A.step->t0 = t;
   A.step->dt32 = (float)d;
   A.step->zero = (d == 0.0);
   if (d > 0.0) {

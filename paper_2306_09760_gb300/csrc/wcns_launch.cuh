@@ -47,6 +47,9 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   A.general = c.general ? 1 : 0;
   A.e = T(c.e); A.c1 = T(c.c1); A.c2 = T(c.c2);
   A.X1 = c.X1; A.X2 = c.X2;
+  if (c.faces) A.f = faces_as<T>(*c.faces);
+  A.cstage = c.cstage;
+  A.tnow = c.tnow;
   return A;
 }
 
@@ -224,8 +227,8 @@ cudaError_t launch_reduce(const GridInfo& g, const void* a, const void* b, int w
 namespace wcns {
 
 template <typename T>
-cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u, int nbins,
-                               unsigned long long* hist, cudaStream_t st) {
+cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<double>& f, const double* tnow,
+                               const void* u, int nbins, unsigned long long* hist, cudaStream_t st) {
   for (int dir = 0; dir < g.ndim; ++dir) {
     HistArgs<T> A{};
     A.u = static_cast<const T*>(u);
@@ -240,6 +243,8 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u
     A.s = scheme_as<T>(s);
     A.rec.hist = hist;
     A.rec.nbins = nbins;
+    A.f = faces_as<T>(f);
+    A.tnow = tnow;
     const int64_t threads = A.lines * A.nk;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     switch (g.nvar) {
@@ -268,8 +273,9 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const void* u
   template cudaError_t launch_adjoint_y<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
                                            cudaStream_t);                                            \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
-  template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const void*, int,       \
-                                             unsigned long long*, cudaStream_t);                     \
+  template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const Faces<double>&,  \
+                                             const double*, const void*, int, unsigned long long*,   \
+                                             cudaStream_t);                                          \
   template cudaError_t launch_reduce<T>(const GridInfo&, const void*, const void*, int, double*, int, \
                                         unsigned int*, double*, cudaStream_t);                       \
   }

@@ -21,6 +21,8 @@ struct HistArgs {
   int64_t kmin, nk;                  // interfaces kmin .. kmin + nk - 1 of every line
   SchemeT<T> s;
   WeightRecorder rec;
+  Faces<T> f;
+  const double* tnow;   // device time (moving-shock faces)
 };
 
 template <typename T, int NV>
@@ -29,16 +31,15 @@ __global__ void __launch_bounds__(256) weight_hist_kernel(HistArgs<T> A) {
   if (idx >= A.lines * A.nk) return;
   const int64_t line = idx / A.nk;
   const int64_t k = A.kmin + (idx - line * A.nk);
+  const double tf = A.f.active ? *A.tnow : 0.0;
   T S[6][NV];
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
-    const int64_t c = ghost(k - 2 + m, A.n, A.bc);
-    const int64_t off = (A.dir == 0) ? line * A.pitch + c : c * A.pitch + line;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       // the y sweep's normal ordering swaps the two momentum components
       const int src = (A.dir == 1 && NV == 4 && v == 1) ? 2 : ((A.dir == 1 && NV == 4 && v == 2) ? 1 : v);
-      S[m][v] = A.u[src * A.fstride + off];
+      S[m][v] = face_cell<T>(A.u, A.pitch, A.fstride, A.dir, line, k - 2 + m, A.n, A.bc, src, A.f, tf);
     }
   }
   T F[NV];

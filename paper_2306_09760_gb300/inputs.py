@@ -178,6 +178,35 @@ def riemann2d(n=2048, seed=0, ny=None):
                    extra={"states": st})
 
 
+# Boundary face types (x-lo, x-hi, y-lo, y-hi) of a Problem's extra["faces"]: 0 the
+# direction's bc, 1 transmissive, 2 inviscid wall, 3 fixed state A, 4 state A for
+# x < wall_x and a wall beyond, 5 moving oblique shock (state A for
+# x < x0 + (y + speed t) dxdy, state B beyond).  States are primitive (rho, u, v, p).
+FACE_GRID, FACE_TRANSMISSIVE, FACE_WALL, FACE_FIXED, FACE_FIXED_THEN_WALL, FACE_SHOCK = range(6)
+
+DMR_POST = (8.0, 7.145, -4.125, 116.5)
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+
+
+def dmr(nx=960, ny=240):
+    """Double Mach reflection (Sec. 4.3, Eq. 37): [0, 4] x [0, 1], a Mach 10 shock through
+    (1/6, 0) at 60 degrees to the wall; pre-shock state below y = sqrt(3) (x - 1/6),
+    post-shock above.  Inflow (post-shock) on the left, outflow on the right, the
+    post-shock state under x < 1/6 and an inviscid wall beyond on the bottom, and the
+    exact moving shock on the top; t_end = 0.2."""
+    x = cell_centres(0.0, 4.0, nx)
+    y = cell_centres(0.0, 1.0, ny)
+    X, Y = np.meshgrid(x, y)
+    pre = Y < np.sqrt(3.0) * (X - 1.0 / 6.0)
+    prim = [np.where(pre, a, b) for a, b in zip(DMR_PRE, DMR_POST)]
+    u0 = prim_to_cons(prim[0], prim[1], prim[2], prim[3], 1.4, 2)
+    faces = {"types": (FACE_FIXED, FACE_TRANSMISSIVE, FACE_FIXED_THEN_WALL, FACE_SHOCK),
+             "state_a": DMR_POST, "state_b": DMR_PRE, "wall_x": 1.0 / 6.0,
+             "shock": (1.0 / 6.0, 1.0 / np.sqrt(3.0), 20.0)}
+    return Problem("dmr", 2, 4, nx, ny, (0.0, 0.0), (4.0, 1.0), (1, 1), u0, 1, t_end=0.2,
+                   extra={"faces": faces})
+
+
 # State ranges of the batched problems.  Drawn as wide as the 2D quadrant states
 # (rho from 0.1, p from 0.03, |u| up to 1), a few percent of the problems are
 # near-vacuum Riemann problems on which the scheme (which has no positivity limiter)

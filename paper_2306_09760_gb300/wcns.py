@@ -55,6 +55,13 @@ class wcns_params(ctypes.Structure):
                 ("harten", ctypes.c_double)]
 
 
+class wcns_faces(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32 * 4),
+                ("state_a", ctypes.c_double * 4), ("state_b", ctypes.c_double * 4),
+                ("wall_x", ctypes.c_double), ("shock_x0", ctypes.c_double),
+                ("shock_dxdy", ctypes.c_double), ("shock_speed", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -80,6 +87,7 @@ def load():
         "wcns_reduce": (st, [vp, vp, vp, ctypes.c_int32, P(ctypes.c_double)]),
         "wcns_adjoint_step": (st, [vp, vp, ctypes.c_double, vp, vp]),
         "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
+        "wcns_set_faces": (st, [vp, vp]),
         "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
         "wcns_status_string": (ctypes.c_char_p, [st]),
@@ -189,6 +197,22 @@ def wcns_weight_hist(ctx, u, nbins: int, hist):
     """App. A weight statistics of one L(u), added into the device uint64 tensor `hist`
     (6 * nbins counters, layout [kind][k][bin])."""
     _check(load().wcns_weight_hist(ctx, _ptr(u), int(nbins), _ptr(hist)), "wcns_weight_hist")
+
+
+def wcns_set_faces(ctx, faces=None):
+    """Boundary faces from a dict {"types": 4 ints, "state_a", "state_b", "wall_x",
+    "shock": (x0, dxdy, speed)} (the layout of inputs' Problem.extra["faces"]); None resets."""
+    if faces is None:
+        _check(load().wcns_set_faces(ctx, None), "wcns_set_faces")
+        return
+    f = wcns_faces()
+    for k in range(4):
+        f.type[k] = int(faces["types"][k])
+        f.state_a[k] = float(faces.get("state_a", (0.0,) * 4)[k])
+        f.state_b[k] = float(faces.get("state_b", (0.0,) * 4)[k])
+    f.wall_x = float(faces.get("wall_x", 0.0))
+    f.shock_x0, f.shock_dxdy, f.shock_speed = (float(v) for v in faces.get("shock", (0.0, 0.0, 0.0)))
+    _check(load().wcns_set_faces(ctx, ctypes.byref(f)), "wcns_set_faces")
 
 
 def wcns_adjoint_step(ctx, u_n, dt: float, lam_np1, lam_n):
@@ -322,6 +346,9 @@ class Solver:
         self.params = make_params(problem.system, self.dtype_code, **kw)
         self.stream = stream
         self.ctx = wcns_init(g, self.params, stream)
+        faces = problem.extra.get("faces") if problem.extra else None
+        if faces:
+            wcns_set_faces(self.ctx, faces)
         self.u = self.alloc()
         self.set_state(problem.u0)
 

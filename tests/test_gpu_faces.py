@@ -1,0 +1,115 @@
+"""Boundary faces on the GPU (wall, inflow, outflow, moving oblique shock; Sec. 4.3)
+against the oracle, on the double Mach reflection and on wall-bounded smooth data."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_09760_gb300 import inputs
+from parity import check64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2306_09760_gb300 import build as wbuild
+    wbuild.build()
+    from paper_2306_09760_gb300 import wcns
+    wcns.load()
+    return wcns
+
+
+def gpu_rhs(W, P, dtype, time=0.0, **params):
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        if time:
+            W.wcns_set_time(S.ctx, time)
+        L = S.numpy(S.rhs()).astype(np.float64)
+        st, _ = S.status()
+        S.close()
+    assert st == W.WCNS_OK
+    return L
+
+
+def gpu_steps(W, P, dtype, nsteps, t_end=0.0, **params):
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        S.step(0.0, nsteps, t_end)
+        u = S.numpy().astype(np.float64)
+        t, taken = S.time()
+        st, _ = S.status()
+        S.close()
+    assert st == W.WCNS_OK, W.wcns_status_string(st)
+    return u, t, taken
+
+
+@pytest.mark.parametrize("family", ["WCNS", "WENO"])
+@pytest.mark.parametrize("time", [0.0, 0.0137])
+def test_dmr_rhs_parity(W, family, time):
+    P = inputs.dmr(240, 60)
+    L = gpu_rhs(W, P, "f64", time=time, family=family)
+    Lr, _ = oracle.rhs(P, family=family, time=time)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family, time=time)[0], P.u0, f"dmr {family} t={time}")
+    L32 = gpu_rhs(W, P, "f32", time=time, family=family)
+    assert np.abs(L32 - Lr).mean() / np.abs(Lr).mean() < 1e-4
+
+
+def test_dmr_steps_parity_f64(W):
+    P = inputs.dmr(240, 60)
+    u, t, taken = gpu_steps(W, P, "f64", 20, family="WENO")
+    ur, tr, takenr, _ = oracle.step(P, nsteps=20, family="WENO")
+    assert taken == takenr == 20 and abs(t - tr) <= 1e-14 * tr
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=20, family="WENO")[0], P.u0, "dmr 20 steps")
+
+
+def test_dmr_full_run_f64_f32(W):
+    """To t = 0.2 on 240 x 60 (about 700 steps) with the FE-WENO family: FP64 under the
+    round-off criterion, FP32 in relative L1, and the top-row shock at its exact place."""
+    P = inputs.dmr(240, 60)
+    u, t, _ = gpu_steps(W, P, "f64", 5000, t_end=0.2, family="WENO")
+    ur, tr, _, _ = oracle.run_to(P, 0.2, family="WENO")
+    assert t == tr == 0.2
+    check64(u, ur, lambda u0: oracle.run_to(P, 0.2, u=u0, family="WENO")[0], P.u0, "dmr t=0.2")
+    u32, t32, _ = gpu_steps(W, P, "f32", 5000, t_end=0.2, family="WENO")
+    assert abs(t32 - 0.2) < 1e-12
+    rel = np.abs(u32 - ur).mean(axis=(1, 2)) / np.abs(ur).mean(axis=(1, 2))
+    assert np.all(rel < 5e-3), rel
+
+
+@pytest.mark.parametrize("family", ["WCNS", "WENO"])
+def test_wall_faces_parity(W, family):
+    P = inputs.random_smooth_euler_2d(96, 80, seed=3)
+    P = inputs.Problem("w", 2, 4, 96, 80, (0.0, 0.0), (1.0, 1.0), (0, 1), P.u0.copy(), 1,
+                       extra={"faces": {"types": (0, 0, inputs.FACE_WALL, inputs.FACE_WALL)}})
+    L = gpu_rhs(W, P, "f64", family=family)
+    Lr, _ = oracle.rhs(P, family=family)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family)[0], P.u0, "walls")
+    u, _, _ = gpu_steps(W, P, "f64", 10, family=family)
+    s0, s1 = P.u0.sum(axis=(1, 2)), u.sum(axis=(1, 2))
+    assert abs(s1[0] - s0[0]) < 1e-12 * abs(s0[0])
+
+
+def test_set_faces_validation(W):
+    import torch
+    P = inputs.random_smooth_euler_2d(32, 32, seed=1)   # periodic in both directions
+    S = W.Solver(P, "f64")
+    for types in ((inputs.FACE_WALL, 0, 0, 0), (0, 0, 9, 0)):
+        with pytest.raises(W.WcnsError) as e:
+            W.wcns_set_faces(S.ctx, {"types": types})
+        assert e.value.status == W.WCNS_ERR_ARG
+    S.close()
+    D = inputs.dmr(64, 16)
+    S = W.Solver(D, "f64", flux="LLF_FROZEN", alpha=(30.0, 30.0))
+    lam = torch.zeros_like(S.u)
+    with pytest.raises(W.WcnsError) as e:
+        W.wcns_adjoint_step(S.ctx, S.u, 1e-5, lam, lam)
+    assert e.value.status == W.WCNS_ERR_UNSUPPORTED
+    W.wcns_set_faces(S.ctx, None)   # back to the grid's transmissive lines
+    W.wcns_adjoint_step(S.ctx, S.u, 1e-5, lam, lam)
+    S.close()
