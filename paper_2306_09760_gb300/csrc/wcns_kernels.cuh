@@ -274,6 +274,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int kRedThreads = 256;
 
+// One 16-byte load of VW consecutive elements (p 16-byte aligned).
+template <typename T, int VW>
+__device__ __forceinline__ void load16(const T* p, T (&out)[VW]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    out[0] = v.x; out[1] = v.y;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // CFL step: max over cells of |u_d| + c per direction, then
 // dt = cfl / sum_d(max_d / h_d), clipped at t_end; the device time advances.
@@ -283,6 +295,7 @@ struct DtArgs {
   const void* u;
   int64_t nx, ny, pitch, fstride;
   int nvar, ndim, system, use_cfl;
+  int bpr;               // blocks per row (1: each block takes whole rows)
   double gamma, cfl, hx, hy, fixed_dt, t_end;
   double adv_wave[2];    // |a_d| for advection
   double* partials;      // 2 * gridDim.x
@@ -304,29 +317,46 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
   int bad = 0;
   if (NV > 1) {
     const T g = T(A.gamma), gm1 = T(A.gamma - 1.0);
-    const int64_t ncell = A.nx * A.ny;
-    // walk the flattened cell index with (row, column) kept incrementally
-    const int64_t stride = (int64_t)gridDim.x * kRedThreads;
-    const int64_t c0 = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
-    const int64_t sj = stride / A.nx, si = stride - sj * A.nx;
-    int64_t j = c0 / A.nx, i = c0 - j * A.nx;
-    for (int64_t c = c0; c < ncell; c += stride) {
-      const int64_t off = j * A.pitch + i;
-      i += si;
-      j += sj;
-      if (i >= A.nx) { i -= A.nx; ++j; }
-      // wave speeds in the state's own precision; the maxima are kept in FP64
-      const T rho = u[off];
-      const T mu = u[A.fstride + off];
-      const T mv = (NV == 4) ? u[2 * A.fstride + off] : T(0);
-      const T E = u[(NV - 1) * A.fstride + off];
-      const T inv = T(1) / rho;
-      const T ux = mu * inv, vy = mv * inv;
-      const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
-      if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
-      const T cs = Num<T>::sqrt_(g * p * inv);
-      mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
-      myT = fmax(myT, Num<T>::abs_(vy) + cs);
+    // 16-byte vectors along the rows (rows start on 128-byte lines, pitch % 32 == 0);
+    // a block takes whole rows, or one chunk of one row when rows are few
+    constexpr int VW = 16 / (int)sizeof(T);
+    const int64_t nvec = (A.nx + VW - 1) / VW;
+    int64_t rbeg, rend, vbeg, vend;
+    if (A.bpr > 1) {
+      rbeg = blockIdx.x / A.bpr;
+      rend = rbeg + 1;
+      const int64_t per = (nvec + A.bpr - 1) / A.bpr;
+      vbeg = (blockIdx.x % A.bpr) * per;
+      vend = min(nvec, vbeg + per);
+    } else {
+      const int64_t rpb = (A.ny + gridDim.x - 1) / gridDim.x;
+      rbeg = (int64_t)blockIdx.x * rpb;
+      rend = min(A.ny, rbeg + rpb);
+      vbeg = 0;
+      vend = nvec;
+    }
+    for (int64_t r = rbeg; r < rend; ++r) {
+      for (int64_t q = vbeg + threadIdx.x; q < vend; q += kRedThreads) {
+        const int64_t off = r * A.pitch + q * VW;
+        T vr[VW], vm[VW], vn[VW], ve[VW];
+        load16<T, VW>(u + off, vr);
+        load16<T, VW>(u + A.fstride + off, vm);
+        if (NV == 4) load16<T, VW>(u + 2 * A.fstride + off, vn);
+        load16<T, VW>(u + (NV - 1) * A.fstride + off, ve);
+#pragma unroll
+        for (int l = 0; l < VW; ++l) {
+          if (q * VW + l >= A.nx) break;
+          // wave speeds in the state's own precision
+          const T rho = vr[l], mu = vm[l], mv = (NV == 4) ? vn[l] : T(0), E = ve[l];
+          const T inv = T(1) / rho;
+          const T ux = mu * inv, vy = mv * inv;
+          const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
+          if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
+          const T cs = Num<T>::sqrt_(g * p * inv);
+          mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
+          myT = fmax(myT, Num<T>::abs_(vy) + cs);
+        }
+      }
     }
   }
   double mx = (double)mxT, my = (double)myT;

@@ -192,11 +192,22 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
   A.adv_wave[0] = d.adv_wave[0]; A.adv_wave[1] = d.adv_wave[1];
   A.partials = d.partials; A.counter = d.counter; A.dt_out = d.dt_out; A.step = d.step; A.t = d.t;
   A.steps = d.steps; A.err = d.err;
-  const int64_t ncell = g.nx * g.ny;
   int blocks = 1;
+  A.bpr = 1;
   if (g.nvar > 1) {
-    int64_t want = (ncell + kRedThreads * 4 - 1) / (kRedThreads * 4);
-    blocks = (int)(want < 1 ? 1 : (want > d.max_blocks ? d.max_blocks : want));
+    // whole rows per block when there are enough rows, else rows split in chunks
+    const int64_t vw = 16 / (int64_t)sizeof(T);
+    const int64_t nvec = (g.nx + vw - 1) / vw;
+    if (g.ny * 2 >= d.max_blocks) {
+      const int64_t rpb = (g.ny + d.max_blocks - 1) / d.max_blocks;
+      blocks = (int)((g.ny + rpb - 1) / rpb);
+    } else {
+      int64_t bpr = d.max_blocks / g.ny;
+      const int64_t useful = (nvec + kRedThreads - 1) / kRedThreads;
+      bpr = bpr < 1 ? 1 : (bpr > useful ? useful : bpr);
+      A.bpr = (int)bpr;
+      blocks = (int)(g.ny * bpr);
+    }
   }
   switch (g.nvar) {
     case 1: dt_kernel<T, 1><<<blocks, kRedThreads, 0, st>>>(A); break;
