@@ -385,6 +385,10 @@ def run_variants(args, W, torch, inputs, hbm_peak):
         out["adjoint_vortex_512"] = run_adjoint_variant(W, torch, inputs)
     except Exception as e:
         out["adjoint_vortex_512"] = {"error": repr(e)}
+    try:
+        out["fp32_error"] = run_fp32_error(W, torch, inputs)
+    except Exception as e:
+        out["fp32_error"] = {"error": repr(e)}
     for name, make, dt, steps, warm, params in cases:
         P = make()
         with torch.cuda.stream(stream):
@@ -395,6 +399,34 @@ def run_variants(args, W, torch, inputs, hbm_peak):
         nbytes = ALG_BYTES_PER_CELL_UPDATE[dt] * P.nvar / 4 if P.nvar != 4 else ALG_BYTES_PER_CELL_UPDATE[dt]
         out[name] = {"value": rate, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
                      "hbm_frac": rate * 1e6 * nbytes / 1e9 / hbm_peak}
+    return out
+
+
+def run_fp32_error(W, torch, inputs):
+    """Error of the FP32 bulk path per config: mean |u_f32 - u_f64| per component over the
+    mean |u_f64|, after the same run (the FP64 path matches the oracle to 1e-11 or its
+    round-off sensitivity, so it stands for it here)."""
+    import numpy as np
+    cases = [
+        ("C1_advection_200_t2", lambda: inputs.advection_sine(200), 400, 0.0),
+        ("C2_sod_4096_t0.2", lambda: inputs.sod(4096), 100000, 0.2),
+        ("C2_shu_osher_4096_t1.8", lambda: inputs.shu_osher(4096), 100000, 1.8),
+        ("C3_riemann2d_512_100steps", lambda: inputs.riemann2d(512, seed=SEED), 100, 0.0),
+        ("C5_vortex_512_200steps", lambda: inputs.vortex(512, seed=0), 200, 0.0),
+    ]
+    out = {}
+    stream = torch.cuda.Stream()
+    for name, make, nsteps, t_end in cases:
+        P = make()
+        res = {}
+        for dt in ("f64", "f32"):
+            with torch.cuda.stream(stream):
+                S = W.Solver(P, dt, stream=stream)
+                S.step(0.0, nsteps, t_end)
+                res[dt] = S.numpy().astype(np.float64)
+                S.close()
+        err = np.abs(res["f32"] - res["f64"]).mean(axis=(1, 2)) / np.abs(res["f64"]).mean(axis=(1, 2))
+        out[name] = [float(e) for e in err]
     return out
 
 

@@ -129,8 +129,13 @@ constexpr int kAYCells = kAYIfc + 5;       // 37
 template <typename T, int NV>
 constexpr size_t adj_y_smem() { return sizeof(T) * NV * (2 * kAYCells + 6 * kAYIfc) * kAYCols; }
 
+// Single precision keeps two 256-thread blocks resident per SM (at most 128 registers);
+// double precision keeps the compiler's choice (a cap would spill).
+template <typename T>
+constexpr int adj_y_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
+
 template <typename T, int NV>
-__global__ void __launch_bounds__(kAYCols * kAYRowsT) adjoint_y_kernel(AdjArgs<T> A) {
+__global__ void __launch_bounds__(kAYCols * kAYRowsT, adj_y_min_blocks<T>()) adjoint_y_kernel(AdjArgs<T> A) {
   constexpr int kYCols = kAYCols, kYRowsT = kAYRowsT, kYPer = kAYPer, kYIfc = kAYIfc, kYTile = kAYTile,
                 kYCells = kAYCells;
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -356,7 +356,9 @@ WCNS_HD T null_distance(T w, const T* n, int k) {
   return d;
 }
 
-template <typename T>
+// FAM = 0: the WCNS control values are compile-time constants (the fixed default
+// configuration); FAM = -1: they are read from the scheme (either family).
+template <typename T, int FAM = -1>
 WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
   bool sat;
   if constexpr (sizeof(T) == 8) {
@@ -383,11 +385,15 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
     w0 = fe_map_slow<T>(0, w0, s); w1 = fe_map_slow<T>(1, w1, s); w2 = fe_map_slow<T>(2, w2, s);
     return;
   }
-  const T g0 = (w0 < s.null0[1]) ? s.ctrl0[0] : s.ctrl0[1];
+  const T c00 = FAM == 0 ? T(1.0 / 16.0) : s.ctrl0[0], c01 = FAM == 0 ? T(1.0 / 6.0) : s.ctrl0[1];
+  const T c10 = FAM == 0 ? T(10.0 / 16.0) : s.ctrl1[0], c11 = FAM == 0 ? T(0.5) : s.ctrl1[1];
+  const T c12 = FAM == 0 ? T(5.0 / 6.0) : s.ctrl1[2];
+  const T c20 = FAM == 0 ? T(5.0 / 16.0) : s.ctrl2[0], c21 = FAM == 0 ? T(0.5) : s.ctrl2[1];
+  const T g0 = (w0 < s.null0[1]) ? c00 : c01;
   w0 = (w0 < s.null0[0] || w0 > s.null0[2]) ? w0 : g0;
-  const T g1 = (w1 < s.null1[1]) ? s.ctrl1[0] : ((w1 < s.null1[2]) ? s.ctrl1[1] : s.ctrl1[2]);
+  const T g1 = (w1 < s.null1[1]) ? c10 : ((w1 < s.null1[2]) ? c11 : c12);
   w1 = (w1 < s.null1[0] || w1 > s.null1[3]) ? w1 : g1;
-  const T g2 = (w2 < s.null2[1]) ? s.ctrl2[0] : s.ctrl2[1];
+  const T g2 = (w2 < s.null2[1]) ? c20 : c21;
   w2 = (w2 < s.null2[0] || w2 > s.null2[2]) ? w2 : g2;
 }
 
@@ -474,7 +480,7 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
       if (!keep) {
         // Eq. 20 on each weight, then renormalised
         T g0 = w0, g1 = w1, g2 = w2;
-        fe_map_all<T>(g0, g1, g2, s);
+        fe_map_all<T, Fixed<FIX>::on ? 0 : -1>(g0, g1, g2, s);
         if (renorm) {
           const T isg = Num<T>::rcp_(g0 + g1 + g2);
           w0 = g0 * isg; w1 = g1 * isg; w2 = g2 * isg;

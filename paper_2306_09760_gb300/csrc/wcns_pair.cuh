@@ -140,8 +140,8 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
                  (r2s >= d2 - cv) && (r2s <= d2 + cv);
       }
       // Eq. 20 on each weight of each lane
-      if (!keep_l) fe_map_all<float>(l0, l1, l2, s);
-      if (!keep_r) fe_map_all<float>(r0s, r1s, r2s, s);
+      if (!keep_l) fe_map_all<float, Fixed<FIX>::on ? 0 : -1>(l0, l1, l2, s);
+      if (!keep_r) fe_map_all<float, Fixed<FIX>::on ? 0 : -1>(r0s, r1s, r2s, s);
       const P2 m0 = mk(l0, r0s), m1 = mk(l1, r1s), m2 = mk(l2, r2s);
       // Eq. 6 on the mapped weights, renormalised (kept lanes are already normalised)
       const P2 acc = fma(m2, q2, fma(m1, q1, mul(m0, q0)));

@@ -1,0 +1,113 @@
+"""Degenerate and extreme grid sizes through the C ABI against the oracle: lines shorter
+than the stencil, single cells, one-row 2D grids, many independent lines, and a line of
+four million cells checked on sampled cells."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_09760_gb300 import inputs
+from parity import check64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2306_09760_gb300 import build as wbuild
+    wbuild.build()
+    from paper_2306_09760_gb300 import wcns
+    wcns.load()
+    return wcns
+
+
+def gpu_rhs(W, P, dtype, **params):
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        L = S.numpy(S.rhs()).astype(np.float64)
+        st, _ = S.status()
+        S.close()
+    assert st == W.WCNS_OK
+    return L
+
+
+def euler1d(n, seed, bc):
+    P = inputs.random_smooth_euler_1d(max(n, 8), seed=seed, periodic=(bc == 0))
+    u0 = P.u0[:, :, :n].copy()
+    return inputs.Problem("tiny", 1, 3, n, 1, (0.0, 0.0), (float(n), 1.0), (bc, bc), u0, 1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 11])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("family", ["WCNS", "WENO"])
+def test_lines_shorter_than_the_stencil(W, n, bc, family):
+    P = euler1d(n, seed=n, bc=bc)
+    L = gpu_rhs(W, P, "f64", family=family)
+    Lr, _ = oracle.rhs(P, family=family)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family)[0], P.u0, f"n={n} bc={bc}")
+    L32 = gpu_rhs(W, P, "f32", family=family)
+    scale = max(np.abs(Lr).mean(), 1e-30)
+    assert np.abs(L32 - Lr).mean() / scale < 1e-4 or np.abs(L32 - Lr).max() < 1e-5 * np.abs(P.u0).max()
+
+
+@pytest.mark.parametrize("n", [1, 4, 6])
+def test_advection_tiny(W, n):
+    x = -1.0 + np.arange(n) * (2.0 / n)
+    P = inputs.Problem("a", 1, 1, n, 1, (-1.0, 0.0), (1.0, 1.0), (0, 0),
+                       np.sin(np.pi * x)[None, None, :].copy() + 0.3, 0, adv_speed=(1.0, 0.0))
+    L = gpu_rhs(W, P, "f64")
+    Lr, _ = oracle.rhs(P)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"adv n={n}")
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (1, 9), (9, 1), (260, 1), (1, 260)])
+def test_thin_2d_grids(W, nx, ny):
+    Q = inputs.random_smooth_euler_2d(max(nx, 8), max(ny, 8), seed=nx * 31 + ny)
+    P = inputs.Problem("thin", 2, 4, nx, ny, (0.0, 0.0), (1.0, 1.0), (1, 0), Q.u0[:, :ny, :nx].copy(), 1)
+    L = gpu_rhs(W, P, "f64")
+    Lr, _ = oracle.rhs(P)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{nx}x{ny}")
+
+
+def test_many_independent_lines(W):
+    """ndim = 1 with ny > 1: every row is its own line (no coupling between rows)."""
+    nx, ny = 300, 517
+    rng = np.random.default_rng(4)
+    lines = [inputs.random_piecewise_euler_1d(nx, seed=int(s)).u0[:, 0, :] for s in rng.integers(0, 10 ** 6, ny)]
+    u0 = np.stack(lines, axis=1)
+    P = inputs.Problem("lines", 1, 3, nx, ny, (0.0, 0.0), (1.0, 1.0), (1, 1), u0, 1)
+    L = gpu_rhs(W, P, "f64")
+    for j in (0, 1, 250, ny - 1):
+        Q = inputs.Problem("line", 1, 3, nx, 1, (0.0, 0.0), (1.0, 1.0), (1, 1), u0[:, j:j + 1, :].copy(), 1)
+        Lr, _ = oracle.rhs(Q)
+        check64(L[:, j:j + 1, :], Lr, lambda v: oracle.rhs(Q, v)[0], Q.u0, f"line {j}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_four_million_cell_line(W, dtype):
+    """A 1D line of 2^22 + 123 cells (ragged last tile), transmissive, with data that varies
+    on the scale of a few hundred cells (unit cells, so single precision still resolves
+    the flux differences): sampled cells against the oracle's per-cell RHS."""
+    n = (1 << 22) + 123
+    i = np.arange(n, dtype=np.float64)
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * i / 517.0) + 0.1 * np.sin(2 * np.pi * i / 91.0)
+    vel = 0.3 * np.sin(2 * np.pi * i / 313.0)
+    p = 1.0 + 0.2 * np.cos(2 * np.pi * i / 211.0)
+    u0 = inputs.prim_to_cons(rho[None, :], vel[None, :], None, p[None, :], 1.4, 1)
+    P = inputs.Problem("long", 1, 3, n, 1, (0.0, 0.0), (float(n), 1.0), (1, 1), u0, 1)
+    L = gpu_rhs(W, P, dtype)
+    rng = np.random.default_rng(3)
+    cells = np.concatenate([rng.integers(0, n, 400), [0, 1, 2, n - 3, n - 2, n - 1]])
+    ref = oracle.rhs_cells(P, P.u0, cells)
+    got = L[:, 0, cells].T
+    if dtype == "f64":
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        if err >= 1e-11:
+            from parity import perturb_ulp
+            sens = np.abs(oracle.rhs_cells(P, perturb_ulp(P.u0), cells) - ref).max() / np.abs(ref).max()
+            assert err < 10 * sens, (err, sens)
+    else:
+        assert np.abs(got - ref).mean() / np.abs(ref).mean() < 1e-4
