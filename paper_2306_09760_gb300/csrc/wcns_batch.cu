@@ -127,9 +127,7 @@ cudaError_t stage_launch(wcns_batch* b, const void* u, const void* un, void* out
   return cudaGetLastError();
 }
 
-bool batch_fixed(const Scheme& s) {
-  return s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1 && s.family == 0;
-}
+bool batch_fixed(const Scheme& s) { return fixed_config(s); }
 
 template <typename T, int FIX>
 cudaError_t stage_fix(wcns_batch* b, int nt, const void* u, const void* un, void* out, double a, double c, int ticket,

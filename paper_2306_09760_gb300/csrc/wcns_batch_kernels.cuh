@@ -57,9 +57,10 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
       const int64_t off = A.off[item.prob];
       const int c0 = item.c0;
       const int ntile = min(TILE, n - c0);
-      for (int idx = t; idx < NV * CELLS; idx += NT) {
-        const int v = idx / CELLS, s = idx - v * CELLS;
-        if (s < ntile + 10) su[v][s] = A.u[v * A.total + off + ghost(c0 - 5 + s, n, A.bc)];
+      for (int s = t; s < ntile + 10; s += NT) {
+        const int64_t gi = off + ghost(c0 - 5 + s, n, A.bc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) su[v][s] = A.u[v * A.total + gi];
       }
       __syncthreads();
       bool fb = false;
@@ -70,8 +71,20 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
 #pragma unroll
           for (int k = 0; k < NV; ++k) S[m][k] = su[k][t + m];
         T F[NV];
-        if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
-        else fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+        if constexpr (sizeof(T) == 4 && NV > 1) {
+          bool exact;
+          fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
+          if (exact) {
+            T E[6][NV];
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+#pragma unroll
+              for (int k = 0; k < NV; ++k) E[m][k] = reload(&su[k][t + m]);
+            fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
+          }
+        } else {
+          fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+        }
 #pragma unroll
         for (int k = 0; k < NV; ++k) sf[k][t] = F[k];
         const bool last = (c0 + TILE >= n);

@@ -134,8 +134,8 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
 
 // Compile-time specialisation of the option switches.  FIX = 0: every option read
 // from the scheme at run time.  FIX = 1: WCNS family, FE weights (Z, p = 1,
-// renormalised), HLLC, characteristic projection -- the default configuration,
-// compiled without the other branches.
+// renormalised, kappa = 0.5), HLLC, characteristic projection -- the default
+// configuration (fixed_config), compiled without the other branches.
 template <int FIX> struct Fixed {
   static constexpr bool on = false;
   static constexpr int weights = 0, flux = 0, characteristic = 0, zp = 1, renorm = 1, family = 0;
@@ -343,21 +343,67 @@ WCNS_HD T fe_map2(T w, const SchemeT<T>& s) {
   return acc + w;
 }
 
-// Eq. 20 for the three weights together.  Where every tanh argument of all three maps
-// is saturated (|xi (w - n)| >= kSat for each null point n), each term is exactly
-// +-amplitude and the sum collapses to a staircase: the identity below the first and
-// above the last null point, the control values of Table 1 (Table B.1 for the WENO
-// family) in between.  That is
-// evaluated by comparisons; otherwise (any argument unsaturated) the exact path runs.
-template <typename T>
-WCNS_HD T null_distance(T w, const T* n, int k) {
-  T d = Num<T>::abs_(w - n[0]);
-  for (int j = 1; j < k; ++j) d = fmin(d, Num<T>::abs_(w - n[j]));
-  return d;
+// Null points of the default configuration (WCNS family, Table 2 rows, kappa = 0.5) as
+// compile-time constants, formed with the same double operations as fill_family_tables.
+WCNS_HD constexpr double fe_null_default(int i, int j) {
+  return i == 0 ? (j == 0 ? 0.5 * (1.0 / 16.0 + 0.0) : j == 1 ? 0.5 * (1.0 / 11.0 + 1.0 / 16.0) : 0.5 * (1.0 + 1.0 / 11.0))
+       : i == 1 ? (j == 0 ? 0.5 * (10.0 / 16.0 + 0.0) : j == 1 ? 0.5 * (2.0 / 3.0 + 10.0 / 16.0)
+                   : j == 2 ? 0.5 * (10.0 / 11.0 + 2.0 / 3.0) : 0.5 * (1.0 + 10.0 / 11.0))
+                : (j == 0 ? 0.5 * (5.0 / 16.0 + 0.0) : j == 1 ? 0.5 * (1.0 / 3.0 + 5.0 / 16.0) : 0.5 * (1.0 + 1.0 / 3.0));
 }
 
-// FAM = 0: the WCNS control values are compile-time constants (the fixed default
-// configuration); FAM = -1: they are read from the scheme (either family).
+// The configuration the FIX = 1 kernels are compiled for: WCNS family, FE weights (Z,
+// p = 1, renormalised) with kappa = 0.5, HLLC, characteristic projection.
+inline bool fixed_config(const Scheme& s) {
+  if (!(s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1 && s.family == 0))
+    return false;
+  for (int j = 0; j < 3; ++j)
+    if (s.null0[j] != fe_null_default(0, j) || s.null2[j] != fe_null_default(2, j)) return false;
+  for (int j = 0; j < 4; ++j)
+    if (s.null1[j] != fe_null_default(1, j)) return false;
+  return true;
+}
+
+// Null point j of map i: a compile-time constant for FAM = 0, else the scheme's.
+template <typename T, int FAM>
+WCNS_HD T fe_null(const SchemeT<T>& s, int i, int j) {
+  if (FAM == 0) return T(fe_null_default(i, j));
+  return i == 0 ? s.null0[j] : (i == 1 ? s.null1[j] : s.null2[j]);
+}
+
+// Smallest |w_i - null| over the ten null points of the three maps.
+template <typename T, int FAM>
+WCNS_HD T fe_null_distance(T w0, T w1, T w2, const SchemeT<T>& s) {
+  T d = fmin(fmin(Num<T>::abs_(w0 - fe_null<T, FAM>(s, 0, 0)), Num<T>::abs_(w0 - fe_null<T, FAM>(s, 0, 1))),
+             Num<T>::abs_(w0 - fe_null<T, FAM>(s, 0, 2)));
+  d = fmin(d, fmin(fmin(Num<T>::abs_(w1 - fe_null<T, FAM>(s, 1, 0)), Num<T>::abs_(w1 - fe_null<T, FAM>(s, 1, 1))),
+                   fmin(Num<T>::abs_(w1 - fe_null<T, FAM>(s, 1, 2)), Num<T>::abs_(w1 - fe_null<T, FAM>(s, 1, 3)))));
+  return fmin(d, fmin(fmin(Num<T>::abs_(w2 - fe_null<T, FAM>(s, 2, 0)), Num<T>::abs_(w2 - fe_null<T, FAM>(s, 2, 1))),
+                      Num<T>::abs_(w2 - fe_null<T, FAM>(s, 2, 2))));
+}
+
+// The saturated map (every tanh term +-1): the identity below the first and above the
+// last null point, the control values of Table 1 (Table B.1) in between.
+template <typename T, int FAM>
+WCNS_HD void fe_staircase(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
+  const T c00 = FAM == 0 ? T(1.0 / 16.0) : s.ctrl0[0], c01 = FAM == 0 ? T(1.0 / 6.0) : s.ctrl0[1];
+  const T c10 = FAM == 0 ? T(10.0 / 16.0) : s.ctrl1[0], c11 = FAM == 0 ? T(0.5) : s.ctrl1[1];
+  const T c12 = FAM == 0 ? T(5.0 / 6.0) : s.ctrl1[2];
+  const T c20 = FAM == 0 ? T(5.0 / 16.0) : s.ctrl2[0], c21 = FAM == 0 ? T(0.5) : s.ctrl2[1];
+  const T g0 = (w0 < fe_null<T, FAM>(s, 0, 1)) ? c00 : c01;
+  w0 = (w0 < fe_null<T, FAM>(s, 0, 0) || w0 > fe_null<T, FAM>(s, 0, 2)) ? w0 : g0;
+  const T g1 = (w1 < fe_null<T, FAM>(s, 1, 1)) ? c10 : ((w1 < fe_null<T, FAM>(s, 1, 2)) ? c11 : c12);
+  w1 = (w1 < fe_null<T, FAM>(s, 1, 0) || w1 > fe_null<T, FAM>(s, 1, 3)) ? w1 : g1;
+  const T g2 = (w2 < fe_null<T, FAM>(s, 2, 1)) ? c20 : c21;
+  w2 = (w2 < fe_null<T, FAM>(s, 2, 0) || w2 > fe_null<T, FAM>(s, 2, 2)) ? w2 : g2;
+}
+
+// Eq. 20 for the three weights together.  Where every tanh argument of all three maps
+// is saturated (|xi (w - n)| >= kSat for each null point n), each term is exactly
+// +-amplitude and the sum collapses to a staircase evaluated by comparisons
+// (fe_staircase); otherwise (any argument unsaturated) the exact path runs.
+// FAM = 0: the default configuration's null points and control values are compile-time
+// constants; FAM = -1: they are read from the scheme (either family).
 template <typename T, int FAM = -1>
 WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
   bool sat;
@@ -375,26 +421,13 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
       w0 = fe_map0<T>(w0, s); w1 = fe_map1<T>(w1, s); w2 = fe_map2<T>(w2, s);
       return;
     }
-    T d = fmin(fmin(fmin(Num<T>::abs_(w0 - s.null0[0]), Num<T>::abs_(w0 - s.null0[1])), Num<T>::abs_(w0 - s.null0[2])),
-               fmin(fmin(Num<T>::abs_(w1 - s.null1[0]), Num<T>::abs_(w1 - s.null1[1])),
-                    fmin(Num<T>::abs_(w1 - s.null1[2]), Num<T>::abs_(w1 - s.null1[3]))));
-    d = fmin(d, fmin(fmin(Num<T>::abs_(w2 - s.null2[0]), Num<T>::abs_(w2 - s.null2[1])), Num<T>::abs_(w2 - s.null2[2])));
-    sat = d >= s.sat_dist;
+    sat = fe_null_distance<T, FAM>(w0, w1, w2, s) >= s.sat_dist;
   }
   if (!sat) {
     w0 = fe_map_slow<T>(0, w0, s); w1 = fe_map_slow<T>(1, w1, s); w2 = fe_map_slow<T>(2, w2, s);
     return;
   }
-  const T c00 = FAM == 0 ? T(1.0 / 16.0) : s.ctrl0[0], c01 = FAM == 0 ? T(1.0 / 6.0) : s.ctrl0[1];
-  const T c10 = FAM == 0 ? T(10.0 / 16.0) : s.ctrl1[0], c11 = FAM == 0 ? T(0.5) : s.ctrl1[1];
-  const T c12 = FAM == 0 ? T(5.0 / 6.0) : s.ctrl1[2];
-  const T c20 = FAM == 0 ? T(5.0 / 16.0) : s.ctrl2[0], c21 = FAM == 0 ? T(0.5) : s.ctrl2[1];
-  const T g0 = (w0 < s.null0[1]) ? c00 : c01;
-  w0 = (w0 < s.null0[0] || w0 > s.null0[2]) ? w0 : g0;
-  const T g1 = (w1 < s.null1[1]) ? c10 : ((w1 < s.null1[2]) ? c11 : c12);
-  w1 = (w1 < s.null1[0] || w1 > s.null1[3]) ? w1 : g1;
-  const T g2 = (w2 < s.null2[1]) ? c20 : c21;
-  w2 = (w2 < s.null2[0] || w2 > s.null2[2]) ? w2 : g2;
+  fe_staircase<T, FAM>(w0, w1, w2, s);
 }
 
 // Eq. 13: Henrick's mapping of a JS weight with ideal value d.
@@ -870,11 +903,12 @@ WCNS_HD T flux_difference_family(int family, T f0, T f1, T f2, T f3, T f4, T f5,
 }
 
 WCNS_HD int64_t ghost(int64_t i, int64_t n, int bc) {
+  if (i >= 0 && i < n) return i;
   if (bc == 0) {
     int64_t r = i % n;
     return r < 0 ? r + n : r;
   }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+  return i < 0 ? 0 : n - 1;
 }
 
 // Double-precision a + b * c rounded in two steps (no contraction), as the positions of

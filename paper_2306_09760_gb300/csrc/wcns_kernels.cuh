@@ -56,6 +56,11 @@ __device__ __forceinline__ double sweep_time(const SweepArgs<T>& A) {
 // then adds b*dt*L_y, so its epilogue reads one array instead of two.
 enum SweepMode { kWriteL = 0, kStage = 1 };
 
+// A second read of a staged value, issued as a fresh shared-memory load so that the
+// first copy need not stay live in registers until the rare path that wants it again.
+template <typename T>
+__device__ __forceinline__ T reload(const T* p) { return *static_cast<const volatile T*>(p); }
+
 __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
   unsigned m = __ballot_sync(0xffffffffu, fb);
   if (m && (threadIdx.x & 31) == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
@@ -98,18 +103,19 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
 #pragma unroll
     for (int k = 0; k < NV; ++k) unv[k] = A.un[k * A.fstride + row * A.pitch + c0 + threadIdx.x];
   }
+  // stage cells c0-5 .. c0+ntile+4 (ntile + 10 <= kXCells), one cell index per thread
+  // and pass, all variables of it
   if (!A.f.active) {
-    for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
-      const int v = idx / kXCells, s = idx - v * kXCells;
-      if (s < ntile + 10) su[idx] = base[v * A.fstride + ghost(c0 - 5 + s, A.nx, A.bc)];
+    for (int s = threadIdx.x; s < ntile + 10; s += kXThreads) {
+      const int64_t gi = ghost(c0 - 5 + s, A.nx, A.bc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) su[v * kXCells + s] = base[v * A.fstride + gi];
     }
   } else {
     const double tf = sweep_time(A);
-    for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
-      const int v = idx / kXCells, s = idx - v * kXCells;
-      if (s < ntile + 10)
-        su[idx] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
-    }
+    for (int s = threadIdx.x; s < ntile + 10; s += kXThreads)
+      for (int v = 0; v < NV; ++v)
+        su[v * kXCells + s] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
   }
   __syncthreads();
   const int t = threadIdx.x;
@@ -121,8 +127,20 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
 #pragma unroll
       for (int k = 0; k < NV; ++k) S[m][k] = su[k * kXCells + t + m];
     T F[NV];
-    if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
-    else fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+    if constexpr (sizeof(T) == 4 && NV > 1) {
+      bool exact;
+      fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
+      if (exact) {
+        T E[6][NV];
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+          for (int k = 0; k < NV; ++k) E[m][k] = reload(su + k * kXCells + t + m);
+        fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
+      }
+    } else {
+      fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
+    }
 #pragma unroll
     for (int k = 0; k < NV; ++k) sf[k * kXThreads + t] = F[k];
     // each interface of the line is counted by exactly one tile
@@ -188,18 +206,25 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
   const int64_t r0 = (int64_t)blockIdx.y * kYTile;
   const int ntile = (int)min((int64_t)kYTile, A.ny - r0);
   const int ncol = (int)min((int64_t)kYCols, A.nx - c0);
-  const int tid = threadIdx.y * kYCols + threadIdx.x;
-  const double tf = sweep_time(A);
-  for (int idx = tid; idx < NV * kYCells * kYCols; idx += kYCols * kYRowsT) {
-    const int x = idx % kYCols;
-    const int rest = idx / kYCols;
-    const int s = rest % kYCells, v = rest / kYCells;
-    if (x < ncol && s < ntile + 10)
-      su[idx] = A.f.active ? face_cell<T>(A.u, A.pitch, A.fstride, 1, c0 + x, r0 - 5 + s, A.ny, A.bc, v, A.f, tf)
-                           : A.u[v * A.fstride + ghost(r0 - 5 + s, A.ny, A.bc) * A.pitch + c0 + x];
+  const int tx = threadIdx.x;
+  // stage rows r0-5 .. r0+ntile+4 (ntile + 10 <= kYCells) of the block's columns: one
+  // row index per thread row and pass, all variables of it
+  if (tx < ncol) {
+    if (!A.f.active) {
+      for (int s = threadIdx.y; s < ntile + 10; s += kYRowsT) {
+        const int64_t gr = ghost(r0 - 5 + s, A.ny, A.bc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) su[(v * kYCells + s) * kYCols + tx] = A.u[v * A.fstride + gr * A.pitch + c0 + tx];
+      }
+    } else {
+      const double tf = sweep_time(A);
+      for (int s = threadIdx.y; s < ntile + 10; s += kYRowsT)
+        for (int v = 0; v < NV; ++v)
+          su[(v * kYCells + s) * kYCols + tx] =
+              face_cell<T>(A.u, A.pitch, A.fstride, 1, c0 + tx, r0 - 5 + s, A.ny, A.bc, v, A.f, tf);
+    }
   }
   __syncthreads();
-  const int tx = threadIdx.x;
   // the sweep's normal ordering swaps the two momentum components
   constexpr int p1 = (NV == 4) ? 2 : 1;
   constexpr int p2 = (NV == 4) ? 1 : 2;
@@ -217,8 +242,24 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
         }
       }
       T F[NV];
-      if constexpr (sizeof(T) == 4 && NV > 1) fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 1, F);
-      else fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
+      if constexpr (sizeof(T) == 4 && NV > 1) {
+        bool exact;
+        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 1, F, exact);
+        if (exact) {
+          T E[6][NV];
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              const int src = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
+              E[m][k] = reload(su + (src * kYCells + t + m) * kYCols + tx);
+            }
+          }
+          fb = interface_flux<T, NV, FIX>(E, A.s, 1, F);
+        }
+      } else {
+        fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
+      }
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const int dst = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);

@@ -11,8 +11,7 @@ namespace wcns {
 // FIX = 1 (compile-time default configuration) applies to the Euler systems only.
 template <int NV>
 static bool use_fixed(const Scheme& s) {
-  return NV > 1 && s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1 &&
-         s.family == 0;
+  return NV > 1 && fixed_config(s);
 }
 
 template <typename T, int NV, int MODE>

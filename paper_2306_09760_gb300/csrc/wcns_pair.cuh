@@ -77,8 +77,10 @@ __device__ __forceinline__ P2 rcp(P2 a) {
 
 // Eq. 5-15 and the option-dependent weight maps for the pair (left, right) of
 // mirrored stencils v0..v4; returns the two interpolated midpoint values (Eq. 6).
+// dmin: lowered to the smallest |w - null| of the FE map's saturated evaluations (Eq. 20);
+// the caller redoes the interface on the exact path when it falls below sat_dist.
 template <int FIX>
-__device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const SchemeT<float>& s) {
+__device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const SchemeT<float>& s, float& dmin) {
   const int weights = WCNS_OPT(FIX, s, weights);
   const int zp = WCNS_OPT(FIX, s, zp);
   const int renorm = WCNS_OPT(FIX, s, renorm);
@@ -139,9 +141,20 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
         keep_r = (r0s >= d0 - cv) && (r0s <= d0 + cv) && (r1s >= d1 - cv) && (r1s <= d1 + cv) &&
                  (r2s >= d2 - cv) && (r2s <= d2 + cv);
       }
-      // Eq. 20 on each weight of each lane
-      if (!keep_l) fe_map_all<float, Fixed<FIX>::on ? 0 : -1>(l0, l1, l2, s);
-      if (!keep_r) fe_map_all<float, Fixed<FIX>::on ? 0 : -1>(r0s, r1s, r2s, s);
+      // Eq. 20 on each weight of each lane: the saturated staircase, with the distance
+      // to the null points kept for one test per interface (the exponential form of the
+      // map at small xi is evaluated here directly)
+      constexpr int FAM = Fixed<FIX>::on ? 0 : -1;
+      if (s.xi_small) {
+        if (!keep_l) fe_map_all<float, FAM>(l0, l1, l2, s);
+        if (!keep_r) fe_map_all<float, FAM>(r0s, r1s, r2s, s);
+      } else {
+        const float dl = keep_l ? 3.0e38f : fe_null_distance<float, FAM>(l0, l1, l2, s);
+        const float dr = keep_r ? 3.0e38f : fe_null_distance<float, FAM>(r0s, r1s, r2s, s);
+        dmin = fminf(dmin, fminf(dl, dr));
+        if (!keep_l) fe_staircase<float, FAM>(l0, l1, l2, s);
+        if (!keep_r) fe_staircase<float, FAM>(r0s, r1s, r2s, s);
+      }
       const P2 m0 = mk(l0, r0s), m1 = mk(l1, r1s), m2 = mk(l2, r2s);
       // Eq. 6 on the mapped weights, renormalised (kept lanes are already normalised)
       const P2 acc = fma(m2, q2, fma(m1, q1, mul(m0, q0)));
@@ -229,13 +242,17 @@ __device__ __forceinline__ RoeAvg<float, NV> roe_pair(const PrimPair<NV>& q, flo
 
 // Midpoint flux at one interface (single precision, Euler systems), the packed
 // counterpart of interface_flux.  Returns true if the interpolated states were
-// non-physical and the interface fell back to (U_i, U_{i+1}).
+// non-physical and the interface fell back to (U_i, U_{i+1}).  Sets `exact` (and leaves
+// F unset) when the interface needs the exact FE map: the caller then calls
+// interface_flux on the same stencil.
 template <int NV, int FIX>
 __device__ __forceinline__ bool interface_flux_pair(const float (&S)[6][NV], const SchemeT<float>& s, int dir,
-                                                   float (&F)[NV]) {
+                                                   float (&F)[NV], bool& exact) {
   static_assert(NV == 3 || NV == 4, "packed path is for the Euler systems");
+  exact = false;
   if (WCNS_OPT(FIX, s, family) == 1) return interface_flux<float, NV, FIX>(S, s, dir, F);  // App. B, scalar
   const float gm1 = s.gm1;
+  float dmin = 3.0e38f;
   P2 U[NV];  // (left, right) interpolated states
   if (WCNS_OPT(FIX, s, characteristic)) {
     P2 Uc[NV];
@@ -255,13 +272,20 @@ __device__ __forceinline__ bool interface_flux_pair(const float (&S)[6][NV], con
     P2 WI[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      WI[k] = weno_pair<FIX>(W[0][k], W[1][k], W[2][k], swap(W[2][k]), swap(W[1][k]), s);
+      WI[k] = weno_pair<FIX>(W[0][k], W[1][k], W[2][k], swap(W[2][k]), swap(W[1][k]), s, dmin);
     unproject_pair<NV>(cb, WI, U);
   } else {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
       U[k] = weno_pair<FIX>(mk(S[0][k], S[5][k]), mk(S[1][k], S[4][k]), mk(S[2][k], S[3][k]),
-                            mk(S[3][k], S[2][k]), mk(S[4][k], S[1][k]), s);
+                            mk(S[3][k], S[2][k]), mk(S[4][k], S[1][k]), s, dmin);
+  }
+  // Some FE tanh term of this interface is not saturated (a weight within sat_dist of a
+  // null point; rare at large xi): the caller runs the interface on the exact scalar
+  // path from its staged stencil (not kept live here).
+  if (!(dmin >= s.sat_dist)) {
+    exact = true;
+    return false;
   }
   // admissibility of the interpolated states (positive density and pressure)
   const PrimPair<NV> q = prim_pair<NV>(U, gm1);
