@@ -67,14 +67,31 @@ __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr
 }
 
 // ---------------------------------------------------------------------------
-// x sweep: one block per (row, tile of XT cells); 256 threads = 256 interfaces.
+// x sweep: one block per (row, tile of cells); 256 threads, P interfaces per thread
+// (interfaces t, t + 256, ...), so a block covers 256 P interfaces and 256 P - 5 cells.
+// kXThreads / kXTile / kXCells are the one-interface-per-thread tile of the adjoint.
 // ---------------------------------------------------------------------------
 constexpr int kXThreads = 256;
 constexpr int kXTile = kXThreads - 5;      // output cells per block
 constexpr int kXCells = kXThreads + 5;     // staged cells per block
 
+// Interfaces per thread: four in single precision (2048^2 x sweep 0.176 ms at one,
+// 0.174 at two, 0.167 at four), one in double precision.
+constexpr int kSweepXPerF32 = 4;
+template <typename T>
+constexpr int sweep_x_per() { return sizeof(T) == 4 ? kSweepXPerF32 : 1; }
+template <typename T>
+constexpr int sweep_x_ifc() { return kXThreads * sweep_x_per<T>(); }   // interfaces per block
+template <typename T>
+constexpr int sweep_x_tile() { return sweep_x_ifc<T>() - 5; }          // output cells per block
+template <typename T>
+constexpr int sweep_x_cells() { return sweep_x_ifc<T>() + 5; }         // staged cells per block
+
+// staged cells, interface fluxes and (P > 1) u^n of the tile's cells
 template <typename T, int NV>
-constexpr size_t sweep_x_smem() { return sizeof(T) * NV * (kXCells + kXThreads); }
+constexpr size_t sweep_x_smem() {
+  return sizeof(T) * NV * (sweep_x_cells<T>() + sweep_x_ifc<T>() + (sweep_x_per<T>() > 1 ? sweep_x_tile<T>() : 0));
+}
 
 // Single-precision sweeps ask for four resident blocks (32 warps per SM, at most 64
 // registers per thread); double precision keeps the compiler's choice.
@@ -83,88 +100,104 @@ constexpr int sweep_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
 
 template <typename T, int NV, int MODE, int FIX>
 __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
+  constexpr int P = sweep_x_per<T>(), IFC = sweep_x_ifc<T>(), TILE = sweep_x_tile<T>(), CELLS = sweep_x_cells<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
-  T* sf = su + NV * kXCells;                // [NV][kXThreads]
+  T* su = reinterpret_cast<T*>(smem_raw);   // [NV][CELLS]
+  T* sf = su + NV * CELLS;                  // [NV][IFC]
+  T* sn = sf + NV * IFC;                    // [NV][TILE] u^n (P > 1)
   T dt = T(0);
   if (A.dt) {
     if (A.dt->zero) return;  // the run has reached t_end: the step changes nothing
     dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
   const int64_t row = blockIdx.y;
-  const int64_t c0 = (int64_t)blockIdx.x * kXTile;
-  const int ntile = (int)min((int64_t)kXTile, A.nx - c0);
+  const int64_t c0 = (int64_t)blockIdx.x * TILE;
+  const int ntile = (int)min((int64_t)TILE, A.nx - c0);
   const T* base = A.u + row * A.pitch;
-  // u^n of this thread's output cell, loaded now so the latency hides under the sweep
+  const bool use_un = MODE == kStage && A.a != T(0);
+  // u^n of the output cells, loaded now so the latency hides under the sweep: in
+  // registers for one cell per thread, staged in shared memory otherwise
   T unv[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) unv[k] = T(0);
-  if (MODE == kStage && A.a != T(0) && (int)threadIdx.x < ntile) {
+  if (P == 1 && use_un && (int)threadIdx.x < ntile) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) unv[k] = A.un[k * A.fstride + row * A.pitch + c0 + threadIdx.x];
   }
-  // stage cells c0-5 .. c0+ntile+4 (ntile + 10 <= kXCells), one cell index per thread
+  if (P > 1 && use_un) {
+    for (int s = threadIdx.x; s < ntile; s += kXThreads)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sn[v * TILE + s] = A.un[v * A.fstride + row * A.pitch + c0 + s];
+  }
+  // stage cells c0-5 .. c0+ntile+4 (ntile + 10 <= CELLS), one cell index per thread
   // and pass, all variables of it
   if (!A.f.active) {
     for (int s = threadIdx.x; s < ntile + 10; s += kXThreads) {
       const int64_t gi = ghost(c0 - 5 + s, A.nx, A.bc);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) su[v * kXCells + s] = base[v * A.fstride + gi];
+      for (int v = 0; v < NV; ++v) su[v * CELLS + s] = base[v * A.fstride + gi];
     }
   } else {
     const double tf = sweep_time(A);
     for (int s = threadIdx.x; s < ntile + 10; s += kXThreads)
       for (int v = 0; v < NV; ++v)
-        su[v * kXCells + s] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
+        su[v * CELLS + s] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
   }
   __syncthreads();
-  const int t = threadIdx.x;
-  bool fb = false;
-  if (t < ntile + 5) {
-    T S[6][NV];
+#pragma unroll 1
+  for (int q = 0; q < P; ++q) {
+    const int t = threadIdx.x + kXThreads * q;
+    bool fb = false;
+    if (t < ntile + 5) {
+      T S[6][NV];
 #pragma unroll
-    for (int m = 0; m < 6; ++m)
+      for (int m = 0; m < 6; ++m)
 #pragma unroll
-      for (int k = 0; k < NV; ++k) S[m][k] = su[k * kXCells + t + m];
-    T F[NV];
-    if constexpr (sizeof(T) == 4 && NV > 1) {
-      bool exact;
-      fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
-      if (exact) {
-        T E[6][NV];
+        for (int k = 0; k < NV; ++k) S[m][k] = su[k * CELLS + t + m];
+      T F[NV];
+      if constexpr (sizeof(T) == 4 && NV > 1) {
+        bool exact;
+        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
+        if (exact) {
+          T E[6][NV];
 #pragma unroll
-        for (int m = 0; m < 6; ++m)
+          for (int m = 0; m < 6; ++m)
 #pragma unroll
-          for (int k = 0; k < NV; ++k) E[m][k] = reload(su + k * kXCells + t + m);
-        fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
+            for (int k = 0; k < NV; ++k) E[m][k] = reload(su + k * CELLS + t + m);
+          fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
+        }
+      } else {
+        fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
       }
-    } else {
-      fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
-    }
 #pragma unroll
-    for (int k = 0; k < NV; ++k) sf[k * kXThreads + t] = F[k];
-    // each interface of the line is counted by exactly one tile
-    const bool owned = (c0 + kXTile >= A.nx) ? true : (t < kXTile);
-    fb = fb && owned;
+      for (int k = 0; k < NV; ++k) sf[k * IFC + t] = F[k];
+      // each interface of the line is counted by exactly one tile
+      const bool owned = (c0 + TILE >= A.nx) ? true : (t < TILE);
+      fb = fb && owned;
+    }
+    count_fallbacks(fb, A.fallbacks);
   }
-  count_fallbacks(fb, A.fallbacks);
   __syncthreads();
-  if (t < ntile) {
+#pragma unroll 1
+  for (int q = 0; q < P; ++q) {
+    const int t = threadIdx.x + kXThreads * q;
+    if (t >= ntile) break;
     const int64_t off = row * A.pitch + c0 + t;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      const T* f = sf + k * kXThreads + t;
+      const T* f = sf + k * IFC + t;
       T L = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[1], f[2], f[3], f[4], f[5], A.inv_h);
       if (MODE == kWriteL) {
         A.out[k * A.fstride + off] = L;
       } else {
-        T cur = su[k * kXCells + t + 5];
+        const T cur = su[k * CELLS + t + 5];
+        const T unk = (P == 1) ? unv[k] : sn[k * TILE + t];
         T v;
         if (!A.general) {
           v = A.b * (cur + dt * L);
-          if (A.a != T(0)) v = A.a * unv[k] + v;
+          if (A.a != T(0)) v = A.a * unk + v;
         } else {
-          v = A.a * unv[k] + A.b * cur + (A.e * dt) * L;
+          v = A.a * unk + A.b * cur + (A.e * dt) * L;
           if (A.X1) v = v + A.c1 * A.X1[k * A.fstride + off];
           if (A.X2) v = v + A.c2 * A.X2[k * A.fstride + off];
         }

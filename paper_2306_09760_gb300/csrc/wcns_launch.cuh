@@ -17,7 +17,7 @@ static bool use_fixed(const Scheme& s) {
 template <typename T, int NV, int MODE>
 static cudaError_t run_sweep_x(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
   const size_t smem = sweep_x_smem<T, NV>();
-  dim3 grid((unsigned)((g.nx + kXTile - 1) / kXTile), (unsigned)g.ny);
+  dim3 grid((unsigned)((g.nx + sweep_x_tile<T>() - 1) / sweep_x_tile<T>()), (unsigned)g.ny);
   if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0)><<<grid, kXThreads, smem, st>>>(A);
   else sweep_x_kernel<T, NV, MODE, 0><<<grid, kXThreads, smem, st>>>(A);
   return cudaGetLastError();

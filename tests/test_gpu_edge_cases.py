@@ -72,6 +72,21 @@ def test_thin_2d_grids(W, nx, ny):
     check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{nx}x{ny}")
 
 
+@pytest.mark.parametrize("nx", [5, 6, 1018, 1019, 1020, 2038, 2039, 2040])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_f32_x_tile_boundaries(W, nx, bc):
+    """Single-precision 2D RHS at and around the x tile of the single-precision sweep
+    (1019 cells: 256 threads with four interfaces each), periodic and transmissive."""
+    Q = inputs.random_smooth_euler_2d(nx, 9, seed=nx + 7 * bc, periodic=(bc == 0))
+    L = gpu_rhs(W, Q, "f32")
+    Lr, _ = oracle.rhs(Q)
+    err = np.abs(L - Lr)
+    assert np.all(np.isfinite(L))
+    assert err.mean() / np.abs(Lr).mean() < 3e-4, err.mean() / np.abs(Lr).mean()
+    # a misplaced cell or ghost would show as an O(|L|) error at the tile edges
+    assert err.max() < 3e-3 * np.abs(Lr).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
 def test_many_independent_lines(W):
     """ndim = 1 with ny > 1: every row is its own line (no coupling between rows)."""
     nx, ny = 300, 517
