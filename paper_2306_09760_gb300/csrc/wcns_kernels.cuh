@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
         A.out[k * A.fstride + off] = L;
       } else {
         const T cur = su[k * CELLS + t + 5];
-        const T unk = (P == 1) ? unv[k] : sn[k * TILE + t];
+        // u^n is staged only when it enters (a != 0); the general form multiplies by a
+        const T unk = (P == 1) ? unv[k] : (use_un ? sn[k * TILE + t] : T(0));
         T v;
         if (!A.general) {
           v = A.b * (cur + dt * L);
