@@ -75,22 +75,20 @@ constexpr int kXThreads = 256;
 constexpr int kXTile = kXThreads - 5;      // output cells per block
 constexpr int kXCells = kXThreads + 5;     // staged cells per block
 
-// Interfaces per thread: four in single precision (2048^2 x sweep 0.176 ms at one,
-// 0.174 at two, 0.167 at four), one in double precision.
-constexpr int kSweepXPerF32 = 4;
-template <typename T>
-constexpr int sweep_x_per() { return sizeof(T) == 4 ? kSweepXPerF32 : 1; }
-template <typename T>
-constexpr int sweep_x_ifc() { return kXThreads * sweep_x_per<T>(); }   // interfaces per block
-template <typename T>
-constexpr int sweep_x_tile() { return sweep_x_ifc<T>() - 5; }          // output cells per block
-template <typename T>
-constexpr int sweep_x_cells() { return sweep_x_ifc<T>() + 5; }         // staged cells per block
+// P interfaces per thread: four for single-precision grids large enough to fill the GPU
+// with such blocks (2048^2 x sweep 0.176 ms at one, 0.174 at two, 0.167 at four), else
+// one (more, shorter blocks for small grids and for double precision).
+template <int P>
+constexpr int sweep_x_ifc() { return kXThreads * P; }   // interfaces per block
+template <int P>
+constexpr int sweep_x_tile() { return sweep_x_ifc<P>() - 5; }          // output cells per block
+template <int P>
+constexpr int sweep_x_cells() { return sweep_x_ifc<P>() + 5; }         // staged cells per block
 
 // staged cells, interface fluxes and (P > 1) u^n of the tile's cells
-template <typename T, int NV>
+template <typename T, int NV, int P>
 constexpr size_t sweep_x_smem() {
-  return sizeof(T) * NV * (sweep_x_cells<T>() + sweep_x_ifc<T>() + (sweep_x_per<T>() > 1 ? sweep_x_tile<T>() : 0));
+  return sizeof(T) * NV * (sweep_x_cells<P>() + sweep_x_ifc<P>() + (P > 1 ? sweep_x_tile<P>() : 0));
 }
 
 // Single-precision sweeps ask for four resident blocks (32 warps per SM, at most 64
@@ -98,9 +96,9 @@ constexpr size_t sweep_x_smem() {
 template <typename T>
 constexpr int sweep_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
 
-template <typename T, int NV, int MODE, int FIX>
+template <typename T, int NV, int MODE, int FIX, int P>
 __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
-  constexpr int P = sweep_x_per<T>(), IFC = sweep_x_ifc<T>(), TILE = sweep_x_tile<T>(), CELLS = sweep_x_cells<T>();
+  constexpr int IFC = sweep_x_ifc<P>(), TILE = sweep_x_tile<P>(), CELLS = sweep_x_cells<P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][CELLS]
   T* sf = su + NV * CELLS;                  // [NV][IFC]

@@ -14,13 +14,35 @@ static bool use_fixed(const Scheme& s) {
   return NV > 1 && fixed_config(s);
 }
 
+template <typename T, int NV, int MODE, int P>
+static cudaError_t run_sweep_x_per(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
+  const size_t smem = sweep_x_smem<T, NV, P>();
+  dim3 grid((unsigned)((g.nx + sweep_x_tile<P>() - 1) / sweep_x_tile<P>()), (unsigned)g.ny);
+  if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0), P><<<grid, kXThreads, smem, st>>>(A);
+  else sweep_x_kernel<T, NV, MODE, 0, P><<<grid, kXThreads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+// SM count of the current device, read by configure_kernels (before any launch or capture).
+inline int& sweep_sm_count() {
+  static int nsm = 0;
+  return nsm;
+}
+
+// Four interfaces per thread (single-precision Euler systems) when the grid gives at
+// least two full waves of such blocks (four per SM), else one.
+inline bool sweep_x_wide(const GridInfo& g) {
+  const int nsm = sweep_sm_count() > 0 ? sweep_sm_count() : 1;
+  const int64_t blocks = g.ny * ((g.nx + sweep_x_tile<4>() - 1) / sweep_x_tile<4>());
+  return blocks >= 2 * 4 * (int64_t)nsm;
+}
+
 template <typename T, int NV, int MODE>
 static cudaError_t run_sweep_x(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
-  const size_t smem = sweep_x_smem<T, NV>();
-  dim3 grid((unsigned)((g.nx + sweep_x_tile<T>() - 1) / sweep_x_tile<T>()), (unsigned)g.ny);
-  if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0)><<<grid, kXThreads, smem, st>>>(A);
-  else sweep_x_kernel<T, NV, MODE, 0><<<grid, kXThreads, smem, st>>>(A);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4 && NV > 1) {
+    if (sweep_x_wide(g)) return run_sweep_x_per<T, NV, MODE, 4>(g, A, fixed, st);
+  }
+  return run_sweep_x_per<T, NV, MODE, 1>(g, A, fixed, st);
 }
 
 template <typename T, int NV, int MODE>
@@ -52,13 +74,22 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   return A;
 }
 
+template <typename T, int NV, int FIX, int P>
+static cudaError_t configure_x() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL, FIX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_x_smem<T, NV, P>())) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage, FIX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sweep_x_smem<T, NV, P>());
+}
+
 template <typename T, int NV, int FIX>
 static cudaError_t configure_fix() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_x_smem<T, NV>())) != cudaSuccess) return e;
+  if ((e = configure_x<T, NV, FIX, 1>()) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4 && NV > 1) {
+    if ((e = configure_x<T, NV, FIX, 4>()) != cudaSuccess) return e;
+  }
   if constexpr (NV == 3) {
     return cudaSuccess;  // no y sweep in 1D Euler
   } else {
@@ -97,6 +128,10 @@ static cudaError_t configure_adjoint() {
 template <typename T>
 cudaError_t configure_kernels(int nvar) {
   cudaError_t e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  sweep_sm_count() = nsm;
   switch (nvar) {
     case 1: return configure_nv<T, 1>();
     case 3:

@@ -72,12 +72,17 @@ def test_thin_2d_grids(W, nx, ny):
     check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{nx}x{ny}")
 
 
-@pytest.mark.parametrize("nx", [5, 6, 1018, 1019, 1020, 2038, 2039, 2040])
+# 1224 rows give at least two waves of four-interface x blocks (1019-cell tiles) on a
+# 152-SM GPU, so those grids take that form; 9 rows keep one interface per thread
+# (251-cell tiles).
+@pytest.mark.parametrize("nx,ny", [(5, 1224), (6, 1224), (1018, 1224), (1019, 1224), (1020, 1224),
+                                   (2038, 1224), (2039, 1224), (2040, 1224),
+                                   (250, 9), (251, 9), (252, 9), (503, 9)])
 @pytest.mark.parametrize("bc", [0, 1])
-def test_f32_x_tile_boundaries(W, nx, bc):
-    """Single-precision 2D RHS at and around the x tile of the single-precision sweep
-    (1019 cells: 256 threads with four interfaces each), periodic and transmissive."""
-    Q = inputs.random_smooth_euler_2d(nx, 9, seed=nx + 7 * bc, periodic=(bc == 0))
+def test_f32_x_tile_boundaries(W, nx, ny, bc):
+    """Single-precision 2D RHS at and around the x tiles of the single-precision sweep,
+    periodic and transmissive."""
+    Q = inputs.random_smooth_euler_2d(nx, ny, seed=nx + 7 * bc, periodic=(bc == 0))
     L = gpu_rhs(W, Q, "f32")
     Lr, _ = oracle.rhs(Q)
     err = np.abs(L - Lr)

@@ -3,8 +3,9 @@
 FP64: relative max error max|gpu - oracle| / max|oracle| <= 1e-11 per run.
 FP32: mean absolute error per component <= 1e-5 (smooth) or 1e-3 (shocked) on states;
       relative L1 <= 1e-4 on single RHS evaluations.
-Sizes span several tiles with ragged tails (x tiles of 251 cells in double and 1019 in
-single precision, y tiles of 75 rows).
+Sizes span several tiles with ragged tails (x tiles of 251 cells, y tiles of 75 rows;
+single-precision grids of at least two waves of blocks take x tiles of 1019 cells, covered
+by the edge-size and full-size tests).
 """
 import numpy as np
 import pytest
@@ -81,7 +82,7 @@ RHS_CASES = [
     ("riemann2d_300x130", lambda: inputs.riemann2d(300, seed=0, ny=130), {}),
     ("riemann2d_eq38_257x131", lambda: inputs.riemann2d(257, seed="eq38", ny=131), {}),
     ("riemann2d_96x400", lambda: inputs.riemann2d(96, seed=1, ny=400), {}),
-    # two single-precision x tiles (1019 cells: four interfaces per thread), the second ragged
+    # five x tiles (251 cells), the last ragged
     ("riemann2d_1100x40", lambda: inputs.riemann2d(1100, seed=2, ny=40), {}),
     ("smooth2d_periodic_300x130", lambda: inputs.random_smooth_euler_2d(300, 130, seed=3), {}),
     ("vortex_64_llf_frozen", lambda: inputs.vortex(64, seed=1), dict(flux="LLF_FROZEN", alpha=(3.0, 3.0), xi=100.0)),
