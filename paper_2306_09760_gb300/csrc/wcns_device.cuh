@@ -134,7 +134,7 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
 
 // Compile-time specialisation of the option switches.  FIX = 0: every option read
 // from the scheme at run time.  FIX = 1: WCNS family, FE weights (Z, p = 1,
-// renormalised, kappa = 0.5), HLLC, characteristic projection -- the default
+// renormalised, kappa = 0.5, xi >= 1e4), HLLC, characteristic projection -- the default
 // configuration (fixed_config), compiled without the other branches.
 template <int FIX> struct Fixed {
   static constexpr bool on = false;
@@ -353,10 +353,12 @@ WCNS_HD constexpr double fe_null_default(int i, int j) {
 }
 
 // The configuration the FIX = 1 kernels are compiled for: WCNS family, FE weights (Z,
-// p = 1, renormalised) with kappa = 0.5, HLLC, characteristic projection.
+// p = 1, renormalised) with kappa = 0.5 and xi >= 1e4, HLLC, characteristic projection.
 inline bool fixed_config(const Scheme& s) {
   if (!(s.weights == 2 && s.flux == 2 && s.characteristic == 1 && s.zp == 1 && s.renorm == 1 && s.family == 0))
     return false;
+  if (s.xi < 1e4) return false;  // single precision evaluates the map differently below 1e4
+
   for (int j = 0; j < 3; ++j)
     if (s.null0[j] != fe_null_default(0, j) || s.null2[j] != fe_null_default(2, j)) return false;
   for (int j = 0; j < 4; ++j)
@@ -417,7 +419,7 @@ WCNS_HD void fe_map_all(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
     d = fminf(d, fminf(fminf(fabsf(c - (float)s.null2[0]), fabsf(c - (float)s.null2[1])), fabsf(c - (float)s.null2[2])));
     sat = xf * d >= 20.0f + 1.0e-4f + 4.0e-7f * xf;
   } else {
-    if (s.xi_small) {
+    if (FAM != 0 && s.xi_small) {  // the default configuration has xi >= 1e4
       w0 = fe_map0<T>(w0, s); w1 = fe_map1<T>(w1, s); w2 = fe_map2<T>(w2, s);
       return;
     }

@@ -145,7 +145,7 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
       // to the null points kept for one test per interface (the exponential form of the
       // map at small xi is evaluated here directly)
       constexpr int FAM = Fixed<FIX>::on ? 0 : -1;
-      if (s.xi_small) {
+      if (!Fixed<FIX>::on && s.xi_small) {
         if (!keep_l) fe_map_all<float, FAM>(l0, l1, l2, s);
         if (!keep_r) fe_map_all<float, FAM>(r0s, r1s, r2s, s);
       } else {
