@@ -42,6 +42,7 @@ struct SweepArgs {
   Faces<T> f;                      // boundary faces beyond periodic / transmissive lines
   double cstage;                   // stage time t0 + cstage * dt of the state read (faces)
   const double* tnow;              // device time (faces, RHS without a step)
+  int row_major;                   // x sweep: blockIdx.x = row, blockIdx.y = tile (else swapped)
 };
 
 // Time of the state a sweep reads, for time-dependent boundary faces.
@@ -108,8 +109,8 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
     if (A.dt->zero) return;  // the run has reached t_end: the step changes nothing
     dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
-  const int64_t row = blockIdx.y;
-  const int64_t c0 = (int64_t)blockIdx.x * TILE;
+  const int64_t row = A.row_major ? blockIdx.x : blockIdx.y;
+  const int64_t c0 = (int64_t)(A.row_major ? blockIdx.y : blockIdx.x) * TILE;
   const int ntile = (int)min((int64_t)TILE, A.nx - c0);
   const T* base = A.u + row * A.pitch;
   const bool use_un = MODE == kStage && A.a != T(0);

@@ -15,9 +15,15 @@ static bool use_fixed(const Scheme& s) {
 }
 
 template <typename T, int NV, int MODE, int P>
-static cudaError_t run_sweep_x_per(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
+static cudaError_t run_sweep_x_per(const GridInfo& g, const SweepArgs<T>& A0, bool fixed, cudaStream_t st) {
   const size_t smem = sweep_x_smem<T, NV, P>();
-  dim3 grid((unsigned)((g.nx + sweep_x_tile<P>() - 1) / sweep_x_tile<P>()), (unsigned)g.ny);
+  const int64_t tiles = (g.nx + sweep_x_tile<P>() - 1) / sweep_x_tile<P>();
+  // Blocks run in order of blockIdx.x first: with rows along x every row's first tiles are
+  // scheduled before any ragged last tile, so the short blocks of the ragged tiles come
+  // last and fill the grid's final partial wave (grid y is limited to 65535).
+  SweepArgs<T> A = A0;
+  A.row_major = tiles <= 65535 ? 1 : 0;
+  dim3 grid = A.row_major ? dim3((unsigned)g.ny, (unsigned)tiles) : dim3((unsigned)tiles, (unsigned)g.ny);
   if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0), P><<<grid, kXThreads, smem, st>>>(A);
   else sweep_x_kernel<T, NV, MODE, 0, P><<<grid, kXThreads, smem, st>>>(A);
   return cudaGetLastError();
