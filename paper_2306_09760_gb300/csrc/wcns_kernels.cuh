@@ -409,26 +409,35 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
       vbeg = 0;
       vend = nvec;
     }
+    // two vectors per thread and pass, both loaded before either is evaluated
     for (int64_t r = rbeg; r < rend; ++r) {
-      for (int64_t q = vbeg + threadIdx.x; q < vend; q += kRedThreads) {
-        const int64_t off = r * A.pitch + q * VW;
-        T vr[VW], vm[VW], vn[VW], ve[VW];
-        load16<T, VW>(u + off, vr);
-        load16<T, VW>(u + A.fstride + off, vm);
-        if (NV == 4) load16<T, VW>(u + 2 * A.fstride + off, vn);
-        load16<T, VW>(u + (NV - 1) * A.fstride + off, ve);
+      for (int64_t q0 = vbeg + threadIdx.x; q0 < vend; q0 += 2 * kRedThreads) {
+        T v[2][NV][VW];
 #pragma unroll
-        for (int l = 0; l < VW; ++l) {
-          if (q * VW + l >= A.nx) break;
-          // wave speeds in the state's own precision
-          const T rho = vr[l], mu = vm[l], mv = (NV == 4) ? vn[l] : T(0), E = ve[l];
-          const T inv = T(1) / rho;
-          const T ux = mu * inv, vy = mv * inv;
-          const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
-          if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
-          const T cs = Num<T>::sqrt_(g * p * inv);
-          mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
-          myT = fmax(myT, Num<T>::abs_(vy) + cs);
+        for (int j = 0; j < 2; ++j) {
+          const int64_t q = q0 + j * kRedThreads;
+          if (q < vend) {
+#pragma unroll
+            for (int w = 0; w < NV; ++w) load16<T, VW>(u + w * A.fstride + r * A.pitch + q * VW, v[j][w]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int64_t q = q0 + j * kRedThreads;
+          if (q >= vend) break;
+#pragma unroll
+          for (int l = 0; l < VW; ++l) {
+            if (q * VW + l >= A.nx) break;
+            // wave speeds in the state's own precision
+            const T rho = v[j][0][l], mu = v[j][1][l], mv = (NV == 4) ? v[j][2][l] : T(0), E = v[j][NV - 1][l];
+            const T inv = T(1) / rho;
+            const T ux = mu * inv, vy = mv * inv;
+            const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
+            if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
+            const T cs = Num<T>::sqrt_(g * p * inv);
+            mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
+            myT = fmax(myT, Num<T>::abs_(vy) + cs);
+          }
         }
       }
     }

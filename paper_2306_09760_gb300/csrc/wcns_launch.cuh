@@ -1,6 +1,8 @@
 // Launchers for one element type T; included once per type by wcns_f32.cu / wcns_f64.cu.
 #pragma once
 
+#include <algorithm>
+
 #include "wcns_internal.h"
 #include "wcns_kernels.cuh"
 #include "wcns_adjoint_kernels.cuh"
@@ -131,6 +133,24 @@ static cudaError_t configure_adjoint() {
   return cudaSuccess;
 }
 
+// Resident blocks of the CFL kernel on the whole GPU (occupancy x SMs), read once.
+template <typename T, int NV>
+static int64_t dt_wave_blocks_nv() {
+  static int64_t cached = 0;
+  if (cached <= 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dt_kernel<T, NV>, kRedThreads, 0) != cudaSuccess ||
+        occ <= 0)
+      occ = 1;
+    cached = (int64_t)occ * (sweep_sm_count() > 0 ? sweep_sm_count() : 1);
+  }
+  return cached;
+}
+template <typename T>
+static int64_t dt_wave_blocks(int nvar) {
+  return nvar == 4 ? dt_wave_blocks_nv<T, 4>() : dt_wave_blocks_nv<T, 3>();
+}
+
 template <typename T>
 cudaError_t configure_kernels(int nvar) {
   cudaError_t e;
@@ -138,6 +158,7 @@ cudaError_t configure_kernels(int nvar) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   sweep_sm_count() = nsm;
+  if (nvar > 1) (void)dt_wave_blocks<T>(nvar);  // occupancy query before any stream capture
   switch (nvar) {
     case 1: return configure_nv<T, 1>();
     case 3:
@@ -235,14 +256,16 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
   int blocks = 1;
   A.bpr = 1;
   if (g.nvar > 1) {
-    // whole rows per block when there are enough rows, else rows split in chunks
+    // whole rows per block when there are enough rows, else rows split in chunks; at
+    // most one wave of resident blocks (a second, partial wave would double the time)
     const int64_t vw = 16 / (int64_t)sizeof(T);
     const int64_t nvec = (g.nx + vw - 1) / vw;
-    if (g.ny * 2 >= d.max_blocks) {
-      const int64_t rpb = (g.ny + d.max_blocks - 1) / d.max_blocks;
+    const int64_t max_blocks = std::min<int64_t>(d.max_blocks, dt_wave_blocks<T>(g.nvar));
+    if (g.ny * 2 >= max_blocks) {
+      const int64_t rpb = (g.ny + max_blocks - 1) / max_blocks;
       blocks = (int)((g.ny + rpb - 1) / rpb);
     } else {
-      int64_t bpr = d.max_blocks / g.ny;
+      int64_t bpr = max_blocks / g.ny;
       const int64_t useful = (nvec + kRedThreads - 1) / kRedThreads;
       bpr = bpr < 1 ? 1 : (bpr > useful ? useful : bpr);
       A.bpr = (int)bpr;
