@@ -30,7 +30,13 @@ UNITS = {
     "wcns_batch.cu": FAST_F32,
     "wcns_noalloc.cu": [],
     "wcns_f64.cu": [],
+    "wcns_f64_x.cu": [],
+    "wcns_f64_y.cu": [],
+    "wcns_f64_adj.cu": [],
     "wcns_f32.cu": FAST_F32,
+    "wcns_f32_x.cu": FAST_F32,
+    "wcns_f32_y.cu": FAST_F32,
+    "wcns_f32_adj.cu": FAST_F32,
 }
 
 

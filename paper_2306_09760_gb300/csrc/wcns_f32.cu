@@ -1,4 +1,3 @@
-// FP32 instantiation of the WCNS-FE kernels (bulk arithmetic in single precision;
-// the reductions accumulate in FP64).
+// F32 instantiation: CFL step, reductions, weight statistics and the kernel configuration.
 #include "wcns_launch.cuh"
-WCNS_INSTANTIATE(float)
+WCNS_INSTANTIATE_MISC(float)

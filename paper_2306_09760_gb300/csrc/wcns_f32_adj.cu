@@ -1,0 +1,3 @@
+// F32 instantiation: adjoint sweeps of one RK step.
+#include "wcns_launch.cuh"
+WCNS_INSTANTIATE_ADJ(float)

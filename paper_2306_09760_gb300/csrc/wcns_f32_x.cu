@@ -1,0 +1,3 @@
+// F32 instantiation: x sweeps (interface fluxes along rows, Eq. 3 difference, RK stage).
+#include "wcns_launch.cuh"
+WCNS_INSTANTIATE_X(float)

@@ -1,3 +1,3 @@
-// FP64 instantiation of the WCNS-FE kernels.
+// F64 instantiation: CFL step, reductions, weight statistics and the kernel configuration.
 #include "wcns_launch.cuh"
-WCNS_INSTANTIATE(double)
+WCNS_INSTANTIATE_MISC(double)

@@ -1,4 +1,4 @@
-// Launchers for one element type T; included once per type by wcns_f32.cu / wcns_f64.cu.
+// Launchers for one element type T; included by the per-type, per-family units wcns_f32*.cu / wcns_f64*.cu.
 #pragma once
 
 #include <algorithm>
@@ -92,30 +92,43 @@ static cudaError_t configure_x() {
 }
 
 template <typename T, int NV, int FIX>
-static cudaError_t configure_fix() {
+static cudaError_t configure_x_fix() {
   cudaError_t e;
   if ((e = configure_x<T, NV, FIX, 1>()) != cudaSuccess) return e;
   if constexpr (sizeof(T) == 4 && NV > 1) {
     if ((e = configure_x<T, NV, FIX, 4>()) != cudaSuccess) return e;
   }
-  if constexpr (NV == 3) {
-    return cudaSuccess;  // no y sweep in 1D Euler
-  } else {
-    if ((e = cudaFuncSetAttribute(sweep_y_kernel<T, NV, kWriteL, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_y_smem<T, NV>())) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_y_kernel<T, NV, kStage, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_y_smem<T, NV>());
-  }
+  return cudaSuccess;
+}
+
+template <typename T, int NV, int FIX>
+static cudaError_t configure_y_fix() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(sweep_y_kernel<T, NV, kWriteL, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_y_smem<T, NV>())) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_y_kernel<T, NV, kStage, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sweep_y_smem<T, NV>());
 }
 
 template <typename T, int NV>
-static cudaError_t configure_nv() {
-  cudaError_t e = configure_fix<T, NV, 0>();
+static cudaError_t configure_x_nv() {
+  cudaError_t e = configure_x_fix<T, NV, 0>();
   if constexpr (NV == 1) {
     return e;
   } else {
     if (e != cudaSuccess) return e;
-    return configure_fix<T, NV, 1>();
+    return configure_x_fix<T, NV, 1>();
+  }
+}
+
+template <typename T, int NV>
+static cudaError_t configure_y_nv() {
+  cudaError_t e = configure_y_fix<T, NV, 0>();
+  if constexpr (NV == 1) {
+    return e;
+  } else {
+    if (e != cudaSuccess) return e;
+    return configure_y_fix<T, NV, 1>();
   }
 }
 
@@ -151,6 +164,38 @@ static int64_t dt_wave_blocks(int nvar) {
   return nvar == 4 ? dt_wave_blocks_nv<T, 4>() : dt_wave_blocks_nv<T, 3>();
 }
 
+// Shared-memory attributes per kernel family; each family's part is instantiated in the
+// translation unit that compiles that family's kernels (wcns_<type>_<family>.cu).
+template <typename T>
+cudaError_t configure_sweep_x(int nvar) {
+  switch (nvar) {
+    case 1: return configure_x_nv<T, 1>();
+    case 3: return configure_x_nv<T, 3>();
+    case 4: return configure_x_nv<T, 4>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t configure_sweep_y(int nvar) {
+  switch (nvar) {
+    case 1: return configure_y_nv<T, 1>();
+    case 3: return cudaSuccess;  // no y sweep in 1D Euler
+    case 4: return configure_y_nv<T, 4>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t configure_adjoints(int nvar) {
+  switch (nvar) {
+    case 1: return cudaSuccess;
+    case 3: return configure_adjoint<T, 3>();
+    case 4: return configure_adjoint<T, 4>();
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t configure_kernels(int nvar) {
   cudaError_t e;
@@ -158,17 +203,11 @@ cudaError_t configure_kernels(int nvar) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   sweep_sm_count() = nsm;
+  if (nvar != 1 && nvar != 3 && nvar != 4) return cudaErrorInvalidValue;
   if (nvar > 1) (void)dt_wave_blocks<T>(nvar);  // occupancy query before any stream capture
-  switch (nvar) {
-    case 1: return configure_nv<T, 1>();
-    case 3:
-      if ((e = configure_nv<T, 3>()) != cudaSuccess) return e;
-      return configure_adjoint<T, 3>();
-    case 4:
-      if ((e = configure_nv<T, 4>()) != cudaSuccess) return e;
-      return configure_adjoint<T, 4>();
-  }
-  return cudaErrorInvalidValue;
+  if ((e = configure_sweep_x<T>(nvar)) != cudaSuccess) return e;
+  if ((e = configure_sweep_y<T>(nvar)) != cudaSuccess) return e;
+  return configure_adjoints<T>(nvar);
 }
 
 template <typename T>
@@ -335,17 +374,42 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
 
 }  // namespace wcns
 
-#define WCNS_INSTANTIATE(T)                                                                          \
+// Explicit instantiations per kernel family.  A unit that instantiates one family declares
+// the others extern, so it compiles none of their kernels.
+#define WCNS_EXTERN_FAMILIES(T)                                                                      \
   namespace wcns {                                                                                   \
-  template cudaError_t configure_kernels<T>(int);                                                    \
+  extern template cudaError_t configure_sweep_x<T>(int);                                             \
+  extern template cudaError_t configure_sweep_y<T>(int);                                             \
+  extern template cudaError_t configure_adjoints<T>(int);                                            \
+  }
+
+#define WCNS_INSTANTIATE_X(T)                                                                        \
+  namespace wcns {                                                                                   \
+  template cudaError_t configure_sweep_x<T>(int);                                                    \
   template cudaError_t launch_sweep_x<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
                                          cudaStream_t);                                              \
+  }
+
+#define WCNS_INSTANTIATE_Y(T)                                                                        \
+  namespace wcns {                                                                                   \
+  template cudaError_t configure_sweep_y<T>(int);                                                    \
   template cudaError_t launch_sweep_y<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
                                          cudaStream_t);                                              \
+  }
+
+#define WCNS_INSTANTIATE_ADJ(T)                                                                      \
+  namespace wcns {                                                                                   \
+  template cudaError_t configure_adjoints<T>(int);                                                   \
   template cudaError_t launch_adjoint_x<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
                                            cudaStream_t);                                            \
   template cudaError_t launch_adjoint_y<T>(const GridInfo&, const Scheme&, const AdjCall<T>&,       \
                                            cudaStream_t);                                            \
+  }
+
+#define WCNS_INSTANTIATE_MISC(T)                                                                     \
+  WCNS_EXTERN_FAMILIES(T)                                                                            \
+  namespace wcns {                                                                                   \
+  template cudaError_t configure_kernels<T>(int);                                                    \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
   template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const Faces<double>&,  \
                                              const double*, const void*, int, unsigned long long*,   \
