@@ -137,11 +137,12 @@ def ncu_traffic(kernel_kind: str):
         return None
 
 
-def flops_per_cell_rhs(problem_small, dtype):
-    """Algorithmic flops of one RHS evaluation per cell (exact operation count of the
-    oracle's plain restatement of the method on the same kind of data)."""
-    import oracle
-    return oracle.count_rhs_flops(problem_small) / (problem_small.nx * problem_small.ny)
+def flops_per_cell_rhs():
+    """Algorithmic flops of one RHS evaluation per cell: the oracle's exact operation count
+    of its plain restatement of the method on a 64 x 64 sample of the same data, stored
+    by oracle/write_flop_counts.py (the timed program runs no oracle code)."""
+    with open(os.path.join(ROOT, "profiles", "algorithmic_flops.json")) as f:
+        return float(json.load(f)["euler2d_riemann_rhs_flops_per_cell"])
 
 
 def cpu_sample_rate(seconds_target=15.0, steps_hint=None):
@@ -307,11 +308,9 @@ def run_ours(args):
         return 0
 
     # dominant kernel and its roofline (algorithmic flops per launch / event duration)
-    import oracle
-    oracle.build()
     dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
     launches, tot_ms = prof[dom]
-    flops_cell = flops_per_cell_rhs(inputs.riemann2d(64, seed=SEED), "f32")
+    flops_cell = flops_per_cell_rhs()
     per_dir = flops_cell / 2.0
     stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0}.get(dom, 0)
     flops_per_launch = ncell * (per_dir + stage_extra)

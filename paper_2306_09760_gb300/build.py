@@ -30,11 +30,15 @@ UNITS = {
     "wcns_batch.cu": FAST_F32,
     "wcns_noalloc.cu": [],
     "wcns_f64.cu": [],
-    "wcns_f64_x.cu": [],
+    "wcns_f64_x1.cu": [],
+    "wcns_f64_x3.cu": [],
+    "wcns_f64_x4.cu": [],
     "wcns_f64_y.cu": [],
     "wcns_f64_adj.cu": [],
     "wcns_f32.cu": FAST_F32,
-    "wcns_f32_x.cu": FAST_F32,
+    "wcns_f32_x1.cu": FAST_F32,
+    "wcns_f32_x3.cu": FAST_F32,
+    "wcns_f32_x4.cu": FAST_F32,
     "wcns_f32_y.cu": FAST_F32,
     "wcns_f32_adj.cu": FAST_F32,
 }

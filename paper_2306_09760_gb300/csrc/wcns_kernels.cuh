@@ -78,18 +78,20 @@ constexpr int kXCells = kXThreads + 5;     // staged cells per block
 
 // P interfaces per thread: four for single-precision grids large enough to fill the GPU
 // with such blocks (2048^2 x sweep 0.176 ms at one, 0.174 at two, 0.167 at four), else
-// one (more, shorter blocks for small grids and for double precision).
-template <int P>
-constexpr int sweep_x_ifc() { return kXThreads * P; }   // interfaces per block
-template <int P>
-constexpr int sweep_x_tile() { return sweep_x_ifc<P>() - 5; }          // output cells per block
-template <int P>
-constexpr int sweep_x_cells() { return sweep_x_ifc<P>() + 5; }         // staged cells per block
+// one (more, shorter blocks for small grids and for double precision).  TH threads per
+// block: 256, or kXNarrow for lines too short to give every SM a 256-thread block.
+constexpr int kXNarrow = 32;
+template <int P, int TH = kXThreads>
+constexpr int sweep_x_ifc() { return TH * P; }   // interfaces per block
+template <int P, int TH = kXThreads>
+constexpr int sweep_x_tile() { return sweep_x_ifc<P, TH>() - 5; }          // output cells per block
+template <int P, int TH = kXThreads>
+constexpr int sweep_x_cells() { return sweep_x_ifc<P, TH>() + 5; }         // staged cells per block
 
 // staged cells, interface fluxes and (P > 1) u^n of the tile's cells
-template <typename T, int NV, int P>
+template <typename T, int NV, int P, int TH = kXThreads>
 constexpr size_t sweep_x_smem() {
-  return sizeof(T) * NV * (sweep_x_cells<P>() + sweep_x_ifc<P>() + (P > 1 ? sweep_x_tile<P>() : 0));
+  return sizeof(T) * NV * (sweep_x_cells<P, TH>() + sweep_x_ifc<P, TH>() + (P > 1 ? sweep_x_tile<P, TH>() : 0));
 }
 
 // Single-precision sweeps ask for four resident blocks (32 warps per SM, at most 64
@@ -97,9 +99,9 @@ constexpr size_t sweep_x_smem() {
 template <typename T>
 constexpr int sweep_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
 
-template <typename T, int NV, int MODE, int FIX, int P>
-__global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
-  constexpr int IFC = sweep_x_ifc<P>(), TILE = sweep_x_tile<P>(), CELLS = sweep_x_cells<P>();
+template <typename T, int NV, int MODE, int FIX, int P, int TH = kXThreads>
+__global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
+  constexpr int IFC = sweep_x_ifc<P, TH>(), TILE = sweep_x_tile<P, TH>(), CELLS = sweep_x_cells<P, TH>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][CELLS]
   T* sf = su + NV * CELLS;                  // [NV][IFC]
@@ -124,28 +126,28 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
     for (int k = 0; k < NV; ++k) unv[k] = A.un[k * A.fstride + row * A.pitch + c0 + threadIdx.x];
   }
   if (P > 1 && use_un) {
-    for (int s = threadIdx.x; s < ntile; s += kXThreads)
+    for (int s = threadIdx.x; s < ntile; s += TH)
 #pragma unroll
       for (int v = 0; v < NV; ++v) sn[v * TILE + s] = A.un[v * A.fstride + row * A.pitch + c0 + s];
   }
   // stage cells c0-5 .. c0+ntile+4 (ntile + 10 <= CELLS), one cell index per thread
   // and pass, all variables of it
   if (!A.f.active) {
-    for (int s = threadIdx.x; s < ntile + 10; s += kXThreads) {
+    for (int s = threadIdx.x; s < ntile + 10; s += TH) {
       const int64_t gi = ghost(c0 - 5 + s, A.nx, A.bc);
 #pragma unroll
       for (int v = 0; v < NV; ++v) su[v * CELLS + s] = base[v * A.fstride + gi];
     }
   } else {
     const double tf = sweep_time(A);
-    for (int s = threadIdx.x; s < ntile + 10; s += kXThreads)
+    for (int s = threadIdx.x; s < ntile + 10; s += TH)
       for (int v = 0; v < NV; ++v)
         su[v * CELLS + s] = face_cell<T>(A.u, A.pitch, A.fstride, 0, row, c0 - 5 + s, A.nx, A.bc, v, A.f, tf);
   }
   __syncthreads();
 #pragma unroll 1
   for (int q = 0; q < P; ++q) {
-    const int t = threadIdx.x + kXThreads * q;
+    const int t = threadIdx.x + TH * q;
     bool fb = false;
     if (t < ntile + 5) {
       T S[6][NV];
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) sweep_x_kern
   __syncthreads();
 #pragma unroll 1
   for (int q = 0; q < P; ++q) {
-    const int t = threadIdx.x + kXThreads * q;
+    const int t = threadIdx.x + TH * q;
     if (t >= ntile) break;
     const int64_t off = row * A.pitch + c0 + t;
 #pragma unroll

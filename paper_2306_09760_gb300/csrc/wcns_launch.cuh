@@ -16,18 +16,18 @@ static bool use_fixed(const Scheme& s) {
   return NV > 1 && fixed_config(s);
 }
 
-template <typename T, int NV, int MODE, int P>
+template <typename T, int NV, int MODE, int P, int TH = kXThreads>
 static cudaError_t run_sweep_x_per(const GridInfo& g, const SweepArgs<T>& A0, bool fixed, cudaStream_t st) {
-  const size_t smem = sweep_x_smem<T, NV, P>();
-  const int64_t tiles = (g.nx + sweep_x_tile<P>() - 1) / sweep_x_tile<P>();
+  const size_t smem = sweep_x_smem<T, NV, P, TH>();
+  const int64_t tiles = (g.nx + sweep_x_tile<P, TH>() - 1) / sweep_x_tile<P, TH>();
   // Blocks run in order of blockIdx.x first: with rows along x every row's first tiles are
   // scheduled before any ragged last tile, so the short blocks of the ragged tiles come
   // last and fill the grid's final partial wave (grid y is limited to 65535).
   SweepArgs<T> A = A0;
   A.row_major = tiles <= 65535 ? 1 : 0;
   dim3 grid = A.row_major ? dim3((unsigned)g.ny, (unsigned)tiles) : dim3((unsigned)tiles, (unsigned)g.ny);
-  if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0), P><<<grid, kXThreads, smem, st>>>(A);
-  else sweep_x_kernel<T, NV, MODE, 0, P><<<grid, kXThreads, smem, st>>>(A);
+  if (fixed) sweep_x_kernel<T, NV, MODE, (NV > 1 ? 1 : 0), P, TH><<<grid, TH, smem, st>>>(A);
+  else sweep_x_kernel<T, NV, MODE, 0, P, TH><<<grid, TH, smem, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -45,12 +45,30 @@ inline bool sweep_x_wide(const GridInfo& g) {
   return blocks >= 2 * 4 * (int64_t)nsm;
 }
 
+// Narrow (kXNarrow-thread) blocks for the one-variable and 1D Euler systems when
+// 256-thread tiles would give fewer blocks than SMs: a line of 4096 cells then spreads
+// over 152 blocks of 27 cells instead of 17 blocks of 251, at 5/27 redundant interfaces.
+inline bool sweep_x_narrow(const GridInfo& g) {
+  const int nsm = sweep_sm_count() > 0 ? sweep_sm_count() : 1;
+  const int64_t blocks = g.ny * ((g.nx + sweep_x_tile<1>() - 1) / sweep_x_tile<1>());
+  return blocks < (int64_t)nsm;
+}
+
 template <typename T, int NV, int MODE>
 static cudaError_t run_sweep_x(const GridInfo& g, const SweepArgs<T>& A, bool fixed, cudaStream_t st) {
   if constexpr (sizeof(T) == 4 && NV > 1) {
     if (sweep_x_wide(g)) return run_sweep_x_per<T, NV, MODE, 4>(g, A, fixed, st);
   }
+  if constexpr (NV < 4) {
+    if (sweep_x_narrow(g)) return run_sweep_x_per<T, NV, MODE, 1, kXNarrow>(g, A, fixed, st);
+  }
   return run_sweep_x_per<T, NV, MODE, 1>(g, A, fixed, st);
+}
+
+// One variable count's x sweeps, instantiated in a unit of its own (wcns_<type>_x<NV>.cu).
+template <typename T, int NV>
+cudaError_t sweep_x_nv(const GridInfo& g, const SweepArgs<T>& A, bool stage, bool fixed, cudaStream_t st) {
+  return stage ? run_sweep_x<T, NV, kStage>(g, A, fixed, st) : run_sweep_x<T, NV, kWriteL>(g, A, fixed, st);
 }
 
 template <typename T, int NV, int MODE>
@@ -82,13 +100,14 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   return A;
 }
 
-template <typename T, int NV, int FIX, int P>
+template <typename T, int NV, int FIX, int P, int TH = kXThreads>
 static cudaError_t configure_x() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL, FIX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_x_smem<T, NV, P>())) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage, FIX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sweep_x_smem<T, NV, P>());
+  if ((e = cudaFuncSetAttribute(sweep_x_kernel<T, NV, kWriteL, FIX, P, TH>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_x_smem<T, NV, P, TH>())) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_x_kernel<T, NV, kStage, FIX, P, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sweep_x_smem<T, NV, P, TH>());
 }
 
 template <typename T, int NV, int FIX>
@@ -97,6 +116,9 @@ static cudaError_t configure_x_fix() {
   if ((e = configure_x<T, NV, FIX, 1>()) != cudaSuccess) return e;
   if constexpr (sizeof(T) == 4 && NV > 1) {
     if ((e = configure_x<T, NV, FIX, 4>()) != cudaSuccess) return e;
+  }
+  if constexpr (NV < 4) {
+    if ((e = configure_x<T, NV, FIX, 1, kXNarrow>()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -111,7 +133,7 @@ static cudaError_t configure_y_fix() {
 }
 
 template <typename T, int NV>
-static cudaError_t configure_x_nv() {
+cudaError_t configure_x_nv() {
   cudaError_t e = configure_x_fix<T, NV, 0>();
   if constexpr (NV == 1) {
     return e;
@@ -254,17 +276,11 @@ cudaError_t launch_adjoint_y(const GridInfo& g, const Scheme& s, const AdjCall<T
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st) {
   SweepArgs<T> A = make_args<T>(g, s, 0, c);
+  // the 2D stage writes the partial stage from the x sweep (same kernel body as kStage)
   switch (g.nvar) {
-    case 1: return c.stage ? run_sweep_x<T, 1, kStage>(g, A, false, st) : run_sweep_x<T, 1, kWriteL>(g, A, false, st);
-    case 3: {
-      const bool f = use_fixed<3>(s);
-      return c.stage ? run_sweep_x<T, 3, kStage>(g, A, f, st) : run_sweep_x<T, 3, kWriteL>(g, A, f, st);
-    }
-    case 4: {
-      // the 2D stage writes the partial stage from the x sweep (same kernel body as kStage)
-      const bool f = use_fixed<4>(s);
-      return c.stage ? run_sweep_x<T, 4, kStage>(g, A, f, st) : run_sweep_x<T, 4, kWriteL>(g, A, f, st);
-    }
+    case 1: return sweep_x_nv<T, 1>(g, A, c.stage, false, st);
+    case 3: return sweep_x_nv<T, 3>(g, A, c.stage, use_fixed<3>(s), st);
+    case 4: return sweep_x_nv<T, 4>(g, A, c.stage, use_fixed<4>(s), st);
   }
   return cudaErrorInvalidValue;
 }
@@ -378,15 +394,23 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
 // the others extern, so it compiles none of their kernels.
 #define WCNS_EXTERN_FAMILIES(T)                                                                      \
   namespace wcns {                                                                                   \
-  extern template cudaError_t configure_sweep_x<T>(int);                                             \
+  extern template cudaError_t configure_x_nv<T, 1>();                                                \
+  extern template cudaError_t configure_x_nv<T, 3>();                                                \
+  extern template cudaError_t configure_x_nv<T, 4>();                                                \
+  extern template cudaError_t sweep_x_nv<T, 1>(const GridInfo&, const SweepArgs<T>&, bool, bool,    \
+                                               cudaStream_t);                                        \
+  extern template cudaError_t sweep_x_nv<T, 3>(const GridInfo&, const SweepArgs<T>&, bool, bool,    \
+                                               cudaStream_t);                                        \
+  extern template cudaError_t sweep_x_nv<T, 4>(const GridInfo&, const SweepArgs<T>&, bool, bool,    \
+                                               cudaStream_t);                                        \
   extern template cudaError_t configure_sweep_y<T>(int);                                             \
   extern template cudaError_t configure_adjoints<T>(int);                                            \
   }
 
-#define WCNS_INSTANTIATE_X(T)                                                                        \
+#define WCNS_INSTANTIATE_X(T, NV)                                                                    \
   namespace wcns {                                                                                   \
-  template cudaError_t configure_sweep_x<T>(int);                                                    \
-  template cudaError_t launch_sweep_x<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
+  template cudaError_t configure_x_nv<T, NV>();                                                      \
+  template cudaError_t sweep_x_nv<T, NV>(const GridInfo&, const SweepArgs<T>&, bool, bool,          \
                                          cudaStream_t);                                              \
   }
 
@@ -410,6 +434,8 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
   WCNS_EXTERN_FAMILIES(T)                                                                            \
   namespace wcns {                                                                                   \
   template cudaError_t configure_kernels<T>(int);                                                    \
+  template cudaError_t launch_sweep_x<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
+                                         cudaStream_t);                                              \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
   template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const Faces<double>&,  \
                                              const double*, const void*, int, unsigned long long*,   \

@@ -131,3 +131,44 @@ def test_four_million_cell_line(W, dtype):
             assert err < 10 * sens, (err, sens)
     else:
         assert np.abs(got - ref).mean() / np.abs(ref).mean() < 1e-4
+
+
+def _line_sizes(kind):
+    """Line lengths around the x sweep's choice of block width: lines whose 256-thread
+    tiles (251 cells) would give fewer blocks than SMs run 32-thread blocks (27 cells)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    return {"narrow_ragged": 27 * 37 + 13, "narrow_widest": (nsm - 1) * 251,
+            "wide_narrowest": nsm * 251, "narrow_one_tile": 27, "narrow_two_tiles": 28}[kind]
+
+
+@pytest.mark.parametrize("kind", ["narrow_ragged", "narrow_widest", "wide_narrowest",
+                                  "narrow_one_tile", "narrow_two_tiles"])
+@pytest.mark.parametrize("system", ["advection", "euler1d"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_x_block_width_choice(W, kind, system, bc):
+    """One-dimensional RHS on both sides of the narrow/wide block choice, FP64 against the
+    oracle (1e-11 or the oracle's own round-off sensitivity) and FP32 by the relative L1
+    bound of the other single-precision line tests."""
+    n = _line_sizes(kind)
+    # periodic data varying over a few hundred cells at every length (unit cells), so
+    # single precision still resolves the flux differences
+    i = np.arange(n, dtype=np.float64)
+    k1, k2, k3 = max(1, n // 300), max(1, n // 97), max(1, n // 211)
+    wave = lambda k, ph: np.sin(2 * np.pi * k * i / n + ph)
+    if system == "euler1d":
+        rho = 1.0 + 0.2 * wave(k1, 0.3) + 0.05 * wave(k2, 1.1)
+        vel = 0.3 * wave(k3, 2.0)
+        p = 1.0 + 0.2 * wave(k2, 0.7)
+        u0 = inputs.prim_to_cons(rho[None, :], vel[None, :], None, p[None, :], 1.4, 1)
+        P = inputs.Problem("line", 1, 3, n, 1, (0.0, 0.0), (float(n), 1.0), (bc, bc), u0, 1)
+    else:
+        u0 = wave(k1, 0.0) + 0.25 * wave(k2, 0.5) + 0.3
+        P = inputs.Problem("a", 1, 1, n, 1, (0.0, 0.0), (float(n), 1.0), (bc, bc), u0[None, None, :].copy(), 0,
+                           adv_speed=(1.0, 0.0))
+    Lr, _ = oracle.rhs(P)
+    L = gpu_rhs(W, P, "f64")
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{system} n={n} bc={bc}")
+    L32 = gpu_rhs(W, P, "f32")
+    assert np.all(np.isfinite(L32))
+    assert np.abs(L32 - Lr).mean() / np.abs(Lr).mean() < 1e-4, np.abs(L32 - Lr).mean() / np.abs(Lr).mean()
