@@ -162,9 +162,15 @@ wcns_status wcns_rhs(wcns_ctx* ctx, const void* u, void* dudt);
  * wcns_set_time) and is read with wcns_get_time.  Asynchronous. */
 wcns_status wcns_step(wcns_ctx* ctx, void* u, double dt, int32_t nsteps, double t_end);
 
-/* wcns_step on a HOST buffer u_host (same layout; pinned memory is fastest): copies
- * it to the context's device state, steps, and copies the result back, all on the
- * context stream; returns after the copy back completes. */
+/* wcns_step on a HOST buffer u_host (same layout), all on the context stream; returns
+ * once u_host holds the result.  Page-locked memory of the context's device (e.g.
+ * cudaHostAlloc) with a 16-byte aligned device address and nvar > 1: the first step's
+ * CFL kernel reads u_host through that address and fills the context's device working
+ * copy as it goes; with nsteps == 1 the last RK stage writes u^(n+1) straight into
+ * u_host, with nsteps > 1 one device-to-host copy brings the working copy back.  Any
+ * other host memory: copied in, stepped, copied back.  Only the nx cells of each row
+ * are guaranteed to be written back.  WCNS_ERR_ARG for a NULL pointer, nsteps < 0 or
+ * a NaN dt/t_end; WCNS_ERR_NOMEM if the working copy cannot be allocated (first call). */
 wcns_status wcns_step_host(wcns_ctx* ctx, void* u_host, double dt, int32_t nsteps, double t_end);
 
 /* Device time control.  wcns_get_time synchronises the stream and returns the

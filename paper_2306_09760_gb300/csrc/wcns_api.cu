@@ -209,9 +209,11 @@ cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double 
   return stage_coef(c, u, un, out, k);
 }
 
-cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool maxwave_only) {
+cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool maxwave_only,
+                      void* copy = nullptr) {
   DtLaunch d{};
   d.u = u;
+  d.copy = copy;
   d.cfl = c->p.cfl;
   d.fixed_dt = dt;
   d.t_end = t_end;
@@ -262,9 +264,13 @@ cudaError_t adjoint_stage(wcns_ctx* c, const void* u, const void* mu, const void
 // form printed as Eq. 16:
 //   u1 = u + dt/2 L(u), u2 = u + dt/2 L(u1), u3 = u + dt L(u2),
 //   u' = -u/3 + u1/3 + 2 u2/3 + u3/3 + dt/6 L(u3).
-cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) {
+//
+// src: where the CFL kernel reads u^n; if it is not u, the kernel also copies it into u
+// (the host-buffer path reads a mapped host buffer once).  out: where the last stage
+// writes u^(n+1) (u itself, or the mapped host buffer).
+cudaError_t rk_step_io(wcns_ctx* c, const void* src, void* u, void* out, double dt, double t_end) {
   cudaError_t e;
-  if ((e = dt_launch(c, u, dt, t_end, false)) != cudaSuccess) return e;
+  if ((e = dt_launch(c, src, dt, t_end, false, src != u ? u : nullptr)) != cudaSuccess) return e;
   if (c->p.integrator == WCNS_RK4) {
     StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.0};
     if ((e = stage_coef(c, u, u, c->u1, k1)) != cudaSuccess) return e;
@@ -273,12 +279,26 @@ cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) {
     StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr, 0.5};
     if ((e = stage_coef(c, c->u2, u, c->u3, k3)) != cudaSuccess) return e;
     StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2, 1.0};
-    return stage_coef(c, c->u3, u, u, k4);
+    return stage_coef(c, c->u3, u, out, k4);
   }
   // stage times t, t + dt, t + dt/2
   if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0, 0.0)) != cudaSuccess) return e;
   if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25, 1.0)) != cudaSuccess) return e;
-  return stage(c, c->u2, u, u, 1.0 / 3.0, 2.0 / 3.0, 0.5);
+  return stage(c, c->u2, u, out, 1.0 / 3.0, 2.0 / 3.0, 0.5);
+}
+
+cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) { return rk_step_io(c, u, u, u, dt, t_end); }
+
+// Device address of page-locked host memory registered in this context, or nullptr
+// (pageable memory, another device's allocation, or a device pointer).
+void* mapped_host(const wcns_ctx* c, void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != c->device) return nullptr;
+  return a.devicePointer;
 }
 
 void drop_graph(wcns_ctx* c) {
@@ -445,12 +465,32 @@ wcns_status wcns_step(wcns_ctx* c, void* u, double dt, int32_t nsteps, double t_
 
 wcns_status wcns_step_host(wcns_ctx* c, void* u_host, double dt, int32_t nsteps, double t_end) {
   if (!c || !u_host || nsteps < 0) return WCNS_ERR_ARG;
+  if (dt != dt || t_end != t_end) return WCNS_ERR_ARG;
   const size_t bytes = c->nelem * c->elem;
   if (!c->host_state) WCNS_TRY(cudaMalloc(&c->host_state, bytes));
-  WCNS_TRY(cudaMemcpyAsync(c->host_state, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
-  wcns_status s = wcns_step(c, c->host_state, dt, nsteps, t_end);
-  if (s != WCNS_OK) return s;
-  WCNS_TRY(cudaMemcpyAsync(u_host, c->host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (nsteps == 0) return WCNS_OK;
+  void* hd = mapped_host(c, u_host);
+  if (!hd || !aligned16(hd) || c->g.nvar == 1) {
+    WCNS_TRY(cudaMemcpyAsync(c->host_state, u_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    wcns_status s = wcns_step(c, c->host_state, dt, nsteps, t_end);
+    if (s != WCNS_OK) return s;
+    WCNS_TRY(cudaMemcpyAsync(u_host, c->host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
+    WCNS_TRY(cudaStreamSynchronize(c->stream));
+    return WCNS_OK;
+  }
+  // Page-locked host buffer: the first step's CFL kernel reads it through its device
+  // address and writes the device working copy as it goes (no separate copy in).  With
+  // one step the last stage writes u^(n+1) straight into the host buffer; with more, the
+  // remaining steps run on the working copy and one copy brings it back (a step frozen
+  // at t_end writes nothing, so the last stage cannot stand in for that copy).
+  if (nsteps == 1) {
+    WCNS_TRY(rk_step_io(c, hd, c->host_state, hd, dt, t_end));
+  } else {
+    WCNS_TRY(rk_step_io(c, hd, c->host_state, c->host_state, dt, t_end));
+    wcns_status s = wcns_step(c, c->host_state, dt, nsteps - 1, t_end);
+    if (s != WCNS_OK) return s;
+    WCNS_TRY(cudaMemcpyAsync(u_host, c->host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
+  }
   WCNS_TRY(cudaStreamSynchronize(c->stream));
   return WCNS_OK;
 }

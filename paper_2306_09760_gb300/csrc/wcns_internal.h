@@ -68,6 +68,7 @@ cudaError_t launch_adjoint_y(const GridInfo& g, const Scheme& s, const AdjCall<T
 
 struct DtLaunch {
   const void* u;
+  void* copy;  // optional: the CFL kernel also copies u here (same layout)
   double cfl, fixed_dt, t_end;
   int use_cfl;
   double adv_wave[2];

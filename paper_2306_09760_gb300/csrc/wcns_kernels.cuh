@@ -362,6 +362,16 @@ __device__ __forceinline__ void load16(const T* p, T (&out)[VW]) {
   }
 }
 
+// One 16-byte store of VW consecutive elements (p 16-byte aligned).
+template <typename T, int VW>
+__device__ __forceinline__ void store16(T* p, const T (&in)[VW]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(in[0], in[1], in[2], in[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(in[0], in[1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // CFL step: max over cells of |u_d| + c per direction, then
 // dt = cfl / sum_d(max_d / h_d), clipped at t_end; the device time advances.
@@ -369,6 +379,7 @@ __device__ __forceinline__ void load16(const T* p, T (&out)[VW]) {
 // ---------------------------------------------------------------------------
 struct DtArgs {
   const void* u;
+  void* copy;            // if set (nvar > 1): every 16-byte vector read from u is stored here too
   int64_t nx, ny, pitch, fstride;
   int nvar, ndim, system, use_cfl;
   int bpr;               // blocks per row (1: each block takes whole rows)
@@ -421,6 +432,11 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
           if (q < vend) {
 #pragma unroll
             for (int w = 0; w < NV; ++w) load16<T, VW>(u + w * A.fstride + r * A.pitch + q * VW, v[j][w]);
+            if (A.copy) {
+#pragma unroll
+              for (int w = 0; w < NV; ++w)
+                store16<T, VW>(static_cast<T*>(A.copy) + w * A.fstride + r * A.pitch + q * VW, v[j][w]);
+            }
           }
         }
 #pragma unroll

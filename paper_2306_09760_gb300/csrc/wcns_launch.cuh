@@ -301,7 +301,7 @@ cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T
 template <typename T>
 cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
   DtArgs A{};
-  A.u = d.u; A.nx = g.nx; A.ny = g.ny; A.pitch = g.pitch; A.fstride = g.ny * g.pitch;
+  A.u = d.u; A.copy = g.nvar > 1 ? d.copy : nullptr; A.nx = g.nx; A.ny = g.ny; A.pitch = g.pitch; A.fstride = g.ny * g.pitch;
   A.nvar = g.nvar; A.ndim = g.ndim; A.use_cfl = d.use_cfl;
   A.gamma = d.gamma; A.cfl = d.cfl; A.hx = g.h[0]; A.hy = g.h[1];
   A.fixed_dt = d.fixed_dt; A.t_end = d.t_end;

@@ -210,17 +210,32 @@ def test_reductions(W, stream):
     np.testing.assert_allclose(mw, oracle.max_wave(P), rtol=1e-14)
 
 
-def test_step_host_equals_step(W, stream):
+@pytest.mark.parametrize("case", ["riemann2d", "sod", "advection"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nsteps", [1, 3])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_host_equals_step(W, stream, case, dtype, nsteps, pinned):
+    """wcns_step_host on page-locked memory (read and written by the kernels through its
+    device address) and on pageable memory (copied) gives bit for bit what wcns_step
+    gives on a device buffer, and leaves the device time where wcns_step leaves it."""
     import torch
-    P = inputs.riemann2d(100, seed=3, ny=70)
-    u_dev, _, _, _ = gpu_steps(W, stream, P, "f64", nsteps=3)
+    P = {"riemann2d": lambda: inputs.riemann2d(100, seed=3, ny=70), "sod": lambda: inputs.sod(300),
+         "advection": lambda: inputs.advection_sine(200)}[case]()
+    u_dev, t_dev, taken_dev, _ = gpu_steps(W, stream, P, dtype, nsteps=nsteps, t_end=0.2)
+    tt = torch.float64 if dtype == "f64" else torch.float32
     with torch.cuda.stream(stream):
-        S = W.Solver(P, "f64", stream=stream)
-        host = torch.zeros((4, 70, S.grid.pitch), dtype=torch.float64).pin_memory()
-        host[:, :, :100] = torch.from_numpy(P.u0)
-        W.wcns_step_host(S.ctx, host, 0.0, 3, 0.0)
+        S = W.Solver(P, dtype, stream=stream)
+        host = torch.full((P.nvar, P.ny, S.grid.pitch), -7.0, dtype=tt)
+        if pinned:
+            host = host.pin_memory()
+        host[:, :, :P.nx] = torch.from_numpy(P.u0).to(tt)
+        W.wcns_step_host(S.ctx, host, 0.0, nsteps, 0.2)
+        t_host, taken_host = S.time()
+        st, _ = S.status()
         S.close()
-    np.testing.assert_array_equal(host[:, :, :100].numpy(), u_dev)
+    assert st == W.WCNS_OK
+    np.testing.assert_array_equal(host[:, :, :P.nx].numpy(), u_dev)
+    assert (t_host, taken_host) == (t_dev, taken_dev)
 
 
 def test_periodic_conservation_gpu(W, stream):
@@ -281,3 +296,27 @@ def test_rk4_eq16_parity(W, stream, make, steps):
     ur, tr, takenr, _ = oracle.step(P, nsteps=steps, rk4=True, cfl=0.3)
     assert taken == takenr == steps and abs(t - tr) <= 1e-13 * tr
     check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=steps, rk4=True, cfl=0.3)[0], P.u0, P.name + " RK4")
+
+
+@pytest.mark.parametrize("case", ["sod_1024", "riemann2d_300x130"])
+def test_parity_growth_curve(W, stream, case):
+    """FP64 GPU against the oracle after 1, 10, 100 steps and at the end of the run: the
+    relative max error at each point is below 1e-11 or within ten times the oracle's own
+    change under a one-ulp input perturbation (the round-off amplification of the
+    nonlinear weights).  The curve is printed (run with -s to see it)."""
+    if case == "sod_1024":
+        P, marks, t_end = inputs.sod(1024), [1, 10, 100, 2000], 0.2
+    else:
+        P, marks, t_end = inputs.riemann2d(300, seed=0, ny=130), [1, 10, 100], 0.0
+    from parity import perturb_ulp, rel_max as rmax
+    curve = []
+    for n in marks:
+        u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=n, t_end=t_end)
+        ur, tr, takenr, _ = oracle.step(P, nsteps=n, t_end=t_end)
+        us, _, _, _ = oracle.step(P, perturb_ulp(P.u0), nsteps=n, t_end=t_end)
+        err, sens = rmax(u, ur), rmax(us, ur)
+        curve.append((taken, err, sens))
+        assert err < 1e-11 or err < 10 * sens, (taken, err, sens)
+        # the CFL steps follow the state, so the time carries the same amplification
+        assert taken == takenr and abs(t - tr) <= max(1e-11, 10 * sens) * tr, (t, tr, sens)
+    print(f"\nparity growth {case}: " + ", ".join(f"step {k}: {e:.2e} (oracle 1-ulp {s:.2e})" for k, e, s in curve))
