@@ -145,9 +145,23 @@ def flops_per_cell_rhs():
         return float(json.load(f)["euler2d_riemann_rhs_flops_per_cell"])
 
 
-def cpu_sample_rate(seconds_target=15.0, steps_hint=None):
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_sample_rate(seconds_target=15.0, steps_hint=None, single_core_seconds=0.0):
     """Times the oracle on a band of the same 2048-wide workload (128 rows around the
-    y = 0.8 quadrant line, transmissive band edges)."""
+    y = 0.8 quadrant line, transmissive band edges), on all host cores and, if
+    single_core_seconds > 0, on one core."""
     import numpy as np
     import oracle
     from paper_2306_09760_gb300 import inputs
@@ -164,9 +178,26 @@ def cpu_sample_rate(seconds_target=15.0, steps_hint=None):
     u, _, _, _ = oracle.step(Q, u, nsteps=steps)
     wall = time.perf_counter() - t0
     cells = Q.nx * Q.ny
-    return {"value": cells * steps / wall / 1e6, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{steps} TVD-RK3 step(s) of a 2048 x 128 band (rows {j0}..{j0 + 127}) of the 2048^2 "
-                      f"workload, FP64 oracle, {wall:.1f} s"}, wall, steps
+    cores = oracle.max_threads()
+    res = {"value": cells * steps / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu": cpu_model(),
+           "sample": f"{steps} TVD-RK3 step(s) of a 2048 x 128 band (rows {j0}..{j0 + 127}) of the 2048^2 "
+                     f"workload, FP64 oracle, {wall:.1f} s"}
+    if single_core_seconds > 0:
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            u1, _, _, _ = oracle.step(Q, band, nsteps=1)
+            one1 = time.perf_counter() - t0
+            steps1 = max(1, int(single_core_seconds / max(one1, 1e-3)))
+            t0 = time.perf_counter()
+            oracle.step(Q, u1, nsteps=steps1)
+            wall1 = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(cores)
+        res["single_core"] = {"value": cells * steps1 / wall1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"{steps1} step(s) of the same band, {wall1:.1f} s"}
+    return res, wall, steps
 
 
 def run_reference(args):
@@ -326,7 +357,7 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu:
-        cpu, _, _ = cpu_sample_rate(seconds_target=args.cpu_seconds)
+        cpu, _, _ = cpu_sample_rate(seconds_target=args.cpu_seconds, single_core_seconds=3.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -519,7 +550,7 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         grads[prec] = g.double()
-        res[prec] = {"J": float(Jv), "forward_s": t1 - t0, "adjoint_s": t2 - t1,
+        res[prec] = {"J": float(Jv.detach()), "forward_s": t1 - t0, "adjoint_s": t2 - t1,
                      "forward_mcells": n * n * steps / (t1 - t0) / 1e6,
                      "adjoint_mcells": n * n * steps / (t2 - t1) / 1e6}
         if prec == "f64":
