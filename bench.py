@@ -290,9 +290,12 @@ def run_ours(args):
 
     P = inputs.riemann2d(N_MAIN, seed=SEED)
     ncell = P.nx * P.ny
+    dtype = args.dtype
+    tdtype = torch.float32 if dtype == "f32" else torch.float64
+    elem = 4 if dtype == "f32" else 8
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        S = W.Solver(P, "f32", stream=stream)
+        S = W.Solver(P, dtype, stream=stream)
         S.step(0.0, args.warmup)
         torch.cuda.synchronize()
         W.wcns_profile_enable(S.ctx, True)
@@ -316,8 +319,8 @@ def run_ours(args):
         t_sim, steps_taken = S.time()
 
         # e2e: the public host-buffer entry point, copies inside the timed region
-        host = torch.zeros((S.grid.nvar, S.grid.ny, S.grid.pitch), dtype=torch.float32).pin_memory()
-        host[:, :, :P.nx] = torch.from_numpy(P.u0).float()
+        host = torch.zeros((S.grid.nvar, S.grid.ny, S.grid.pitch), dtype=tdtype).pin_memory()
+        host[:, :, :P.nx] = torch.from_numpy(P.u0).to(tdtype)
         e2e_steps = max(1, min(args.steps, 10))
         W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
         barrier()
@@ -331,7 +334,7 @@ def run_ours(args):
     ms_max, e2e_max = max_over_ranks([ms, e2e_wall], world, device="cuda")
     value = whole_job_rate(world, ncell, args.steps, ms_max / 1e3)
     e2e_value = whole_job_rate(world, ncell, e2e_steps, e2e_max)
-    state_bytes = S.grid.nvar * S.grid.ny * S.grid.pitch * 4
+    state_bytes = S.grid.nvar * S.grid.ny * S.grid.pitch * elem
 
     if rank != 0:
         if world > 1:
@@ -347,8 +350,11 @@ def run_ours(args):
     flops_per_launch = ncell * (per_dir + stage_extra)
     achieved_tflops = flops_per_launch / (tot_ms / launches / 1e3) / 1e12
     hbm_peak, hbm_kind = measured_peaks()
-    alg_gbs = value * 1e6 * ALG_BYTES_PER_CELL_UPDATE["f32"] / 1e9
-    traffic = ncu_traffic(dom)
+    alg_gbs = value * 1e6 * ALG_BYTES_PER_CELL_UPDATE[dtype] / 1e9
+    alu_peak = FP32_ALU_PEAK_TFLOPS if dtype == "f32" else FP64_ALU_PEAK_TFLOPS
+    alu_src = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if dtype == "f32"
+               else "nominal GB300 FP64 rate (a probe measured 1.20 TFLOP/s)")
+    traffic = ncu_traffic(dom) if dtype == "f32" else None
     gpu_launches = sum(v[0] for v in prof.values())
 
     variants = {}
@@ -362,19 +368,20 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": dtype, "data": "synthetic",
         "config": {"workload": "2D Euler 2048x2048, four-quadrant Riemann data (seed 0, split x=y=0.8), "
-                               "transmissive, CFL 0.5, WCNS-FE (xi=1e6, kappa=0.5), HLLC, characteristic; FP32 bulk",
+                               "transmissive, CFL 0.5, WCNS-FE (xi=1e6, kappa=0.5), HLLC, characteristic; "
+                               + ("FP32 bulk" if dtype == "f32" else "FP64"),
                    "global_batch": world, "seq_len": N_MAIN, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2: each stage touches 4 state-size arrays (256 MiB) > 126 MiB L2",
                    "simulated_time": t_sim, "steps_taken": steps_taken, "fallback_interfaces": nonph},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP32_ALU_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": traffic,
+                     "peak_source": alu_src,
                      "flops_per_launch": flops_per_launch, "launch_ms": tot_ms / launches},
         "hbm": {"achieved_gbs": alg_gbs, "peak_gbs": hbm_peak, "frac": alg_gbs / hbm_peak,
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE["f32"]},
+                "bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE[dtype]},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},
@@ -580,6 +587,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"],
+                    help="element type of the main line (default f32: FP32 bulk arithmetic)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
