@@ -482,3 +482,174 @@ def test_app_a_fe_weights_raise_the_ideal_share():
     for k, d in enumerate((1 / 16, 10 / 16, 5 / 16)):
         b = int(d * nb)
         assert H[1, k, b] > 1.3 * H[0, k, b], (k, H[0, k, b] / tot, H[1, k, b] / tot)
+
+
+# ---------------------------------------------------------------------------
+# JS weights (Eq. 11) and M weights (Eq. 12-13), pinned in exact rational arithmetic
+# ---------------------------------------------------------------------------
+def _quadratic_derivatives_at_xi(nodes, vals):
+    """First and second derivative at x = 0 (x_i, h = 1) of the quadratic through
+    (nodes, vals), from the Lagrange form in exact fractions.  Eq. 10's f_{i,k} and
+    s_{i,k} are these derivatives on the sub-stencil S_k."""
+    d1 = Fraction(0)
+    d2 = Fraction(0)
+    for a, (xa, ya) in enumerate(zip(nodes, vals)):
+        others = [xb for b, xb in enumerate(nodes) if b != a]
+        den = Fraction(1)
+        for xb in others:
+            den *= xa - xb
+        # l_a(x) = (x - o0)(x - o1) / den: l_a'(0) = -(o0 + o1) / den, l_a'' = 2 / den
+        d1 += ya * Fraction(-(others[0] + others[1])) / den
+        d2 += ya * Fraction(2) / den
+    return d1, d2
+
+
+def _js_weights_exact(v, eps, ideal=(Fraction(1, 16), Fraction(10, 16), Fraction(5, 16))):
+    """Eq. 9 with the derivatives of Eq. 10 taken from the sub-stencil quadratics, then
+    Eq. 11: alpha_k = d_k / (IS_k + eps)^2, normalised over k = 0..2."""
+    v = [Fraction(x) for x in v]
+    eps = Fraction(eps)
+    alphas = []
+    for k in range(3):
+        nodes = [k - 2, k - 1, k]
+        f, s = _quadratic_derivatives_at_xi(nodes, v[k:k + 3])
+        IS = f * f + s * s
+        alphas.append(ideal[k] / ((IS + eps) ** 2))
+    tot = sum(alphas)
+    return [a / tot for a in alphas], alphas
+
+
+def _eq8_weights_exact(v, eps):
+    """The garbled Eq. 8 form d_k / (IS_k^2 + eps): a plausible misreading of Eq. 11."""
+    v = [Fraction(x) for x in v]
+    eps = Fraction(eps)
+    ideal = (Fraction(1, 16), Fraction(10, 16), Fraction(5, 16))
+    alphas = []
+    for k in range(3):
+        f, s = _quadratic_derivatives_at_xi([k - 2, k - 1, k], v[k:k + 3])
+        IS = f * f + s * s
+        alphas.append(ideal[k] / (IS * IS + eps))
+    tot = sum(alphas)
+    return [a / tot for a in alphas]
+
+
+JS_STENCILS = [
+    # (values u_{i-2}..u_{i+2}, eps): a quadratic with a jump between i and i+1, a kink,
+    # a step at the left end, and a smooth cubic -- each with an eps that is not
+    # negligible against IS, so the place of eps in Eq. 11 matters
+    ([Fraction(0), Fraction(1, 10), Fraction(2, 5), Fraction(5, 2), Fraction(18, 5)], Fraction(1, 4)),
+    ([Fraction(1), Fraction(1), Fraction(1), Fraction(3, 2), Fraction(2)], Fraction(1, 100)),
+    ([Fraction(3), Fraction(0), Fraction(1, 8), Fraction(1, 2), Fraction(3, 2)], Fraction(1, 10)),
+    ([Fraction(-8, 10), Fraction(-1, 10), Fraction(0), Fraction(1, 10), Fraction(8, 10)], Fraction(1, 1000)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(JS_STENCILS)))
+def test_js_weights_eq11_exact(case):
+    """Eq. 11 (Sec. 2): omega_k = alpha_k / sum_l alpha_l with alpha_k = d_k / (IS_k + eps)^2,
+    IS_k from Eq. 9-10 -- the oracle's base weights agree with the exact rational value to
+    1e-15, and differ from the Eq. 8 form d_k / (IS_k^2 + eps) on the same stencil."""
+    v, eps = JS_STENCILS[case]
+    want, _ = _js_weights_exact(v, eps)
+    _, wz, wf, mapped = oracle.interp([float(x) for x in v], weights="JS", eps=float(eps))
+    assert mapped == 0
+    np.testing.assert_allclose(wz, [float(w) for w in want], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(wz, wf)  # JS weights are final as they are
+    other = _eq8_weights_exact(v, eps)
+    assert max(abs(float(a - b)) for a, b in zip(want, other)) > 1e-3, "stencil does not tell Eq. 8 from Eq. 11"
+
+
+@pytest.mark.parametrize("case", range(len(JS_STENCILS)))
+def test_m_weights_eq12_13_exact(case):
+    """Eq. 12-13: the M weights map the JS weights with Henrick's g_k and renormalise;
+    checked against the exact rational evaluation on the Eq. 11 stencils."""
+    v, eps = JS_STENCILS[case]
+    js, _ = _js_weights_exact(v, eps)
+    ideal = (Fraction(1, 16), Fraction(10, 16), Fraction(5, 16))
+    g = [w * (d + d * d - 3 * d * w + w * w) / (d * d + (1 - 2 * d) * w) for w, d in zip(js, ideal)]
+    tot = sum(g)
+    want = [float(x / tot) for x in g]
+    _, wz, wf, _ = oracle.interp([float(x) for x in v], weights="M", eps=float(eps))
+    np.testing.assert_allclose(wz, [float(w) for w in js], rtol=0, atol=1e-15)  # base = JS
+    np.testing.assert_allclose(wf, want, rtol=0, atol=1e-15)
+
+
+def test_js_interpolated_value_exact():
+    """Eq. 6 with the Eq. 11 weights and the Eq. 5 sub-stencil values, each sub-stencil
+    value formed independently as the quadratic interpolant at x_{i+1/2}."""
+    v, eps = JS_STENCILS[0]
+    w, _ = _js_weights_exact(v, eps)
+    q = []
+    for k in range(3):
+        nodes = [k - 2, k - 1, k]
+        val = Fraction(0)
+        for a, xa in enumerate(nodes):
+            term = v[k + a]
+            for b, xb in enumerate(nodes):
+                if b != a:
+                    term *= (Fraction(1, 2) - xb) / Fraction(xa - xb)
+            val += term
+        q.append(val)
+    want = float(sum(wk * qk for wk, qk in zip(w, q)))
+    got, _, _, _ = oracle.interp([float(x) for x in v], weights="JS", eps=float(eps))
+    assert abs(got - want) <= 4e-16 * max(1.0, abs(want))
+
+
+# ---------------------------------------------------------------------------
+# CFL step (Sec. 4 marches at a CFL number; the hot path's rule dt = cfl / sum_d max/h_d)
+# ---------------------------------------------------------------------------
+def test_cfl_step_advection_c1_exact():
+    """Scalar advection, speed 1, h = 0.01, CFL 0.5: dt = 0.5 * 0.01 / 1 = 0.005, so one
+    CFL step ends at t = 0.005 and 400 steps reach t = 2 up to the rounding of 400 sums
+    (0.005 has no exact binary form: a 401st step of round-off size may close the gap)."""
+    P = inputs.advection_sine(200)
+    _, t, taken, _ = oracle.step(P, dt=0.0, nsteps=1, cfl=0.5)
+    assert taken == 1 and abs(t - 0.005) <= 1e-18
+    _, t, taken, _ = oracle.step(P, dt=0.0, nsteps=400, cfl=0.5)
+    assert taken == 400 and abs(t - 2.0) <= 400 * 2.0 ** -52 * 2.0
+    _, t, taken, _ = oracle.step(P, dt=0.0, nsteps=10 ** 6, t_end=2.0, cfl=0.5)
+    assert taken in (400, 401) and t == 2.0
+
+
+def test_cfl_step_sod_closed_form():
+    """Sod tube: the fastest initial signal is the left state's sound speed sqrt(1.4),
+    so the first CFL step is cfl * h / sqrt(gamma p_L / rho_L) = 0.5 (1/N) / sqrt(1.4)."""
+    n = 512
+    P = inputs.sod(n)
+    wx, _ = oracle.max_wave(P)
+    assert abs(wx - math.sqrt(1.4)) <= 1e-15
+    _, t, _, _ = oracle.step(P, dt=0.0, nsteps=1, cfl=0.5)
+    want = 0.5 * (1.0 / n) / math.sqrt(1.4)
+    assert abs(t - want) <= 1e-15 * want
+    # CFL 0.3 (the paper's choice, Sec. 4) scales the step linearly
+    _, t3, _, _ = oracle.step(P, dt=0.0, nsteps=1, cfl=0.3)
+    assert abs(t3 - 0.6 * want) <= 1e-15 * want
+
+
+def test_cfl_step_2d_sums_both_directions():
+    """2D: dt = cfl / ((|u| + c) / hx + (|v| + c) / hy) on a uniform state with u != v and
+    hx != hy (a mistake in either term or a max in place of the sum changes it)."""
+    nx, ny = 48, 40
+    rho, u, v, p, gamma = 1.3, 0.7, -0.2, 0.9, 1.4
+    c = math.sqrt(gamma * p / rho)
+    u0 = inputs.prim_to_cons(np.full((ny, nx), rho), np.full((ny, nx), u), np.full((ny, nx), v),
+                             np.full((ny, nx), p), gamma, 2)
+    P = inputs.Problem("uniform2d", 2, 4, nx, ny, (0.0, 0.0), (2.0, 0.5), (1, 1), u0, 1)
+    hx, hy = 2.0 / nx, 0.5 / ny
+    wx, wy = oracle.max_wave(P)
+    assert abs(wx - (abs(u) + c)) <= 1e-15 and abs(wy - (abs(v) + c)) <= 1e-15
+    _, t, _, _ = oracle.step(P, dt=0.0, nsteps=1, cfl=0.5)
+    want = 0.5 / ((abs(u) + c) / hx + (abs(v) + c) / hy)
+    assert abs(t - want) <= 2e-15 * want
+
+
+def test_cfl_step_clipped_at_t_end():
+    """t_end clips the last step so the run ends on t_end exactly and stops there (a
+    uniform periodic flow keeps max(|u| + c), hence the CFL step, constant)."""
+    n, rho, u, p = 256, 1.0, 0.5, 1.0
+    u0 = inputs.prim_to_cons(np.full((1, n), rho), np.full((1, n), u), None, np.full((1, n), p), 1.4, 1)
+    P = inputs.Problem("uniform1d", 1, 3, n, 1, (0.0, 0.0), (1.0, 1.0), (0, 0), u0, 1)
+    dt0 = 0.5 * (1.0 / n) / (u + math.sqrt(1.4 * p / rho))
+    t_end = 2.5 * dt0
+    _, t, taken, _ = oracle.step(P, dt=0.0, nsteps=10, t_end=t_end, cfl=0.5)
+    assert t == t_end and taken == 3
