@@ -216,17 +216,22 @@ wcns_status wcns_set_faces(wcns_ctx* ctx, const wcns_faces* faces);
  * framework whose allocator owns the device memory -- and therefore cannot create a
  * wcns_ctx either.  Its scratch is one 64 KiB array in device memory that every GPU
  * loading the library holds until the process exits.
- *   grid:   layout of a and b (nvar <= 4; dtype, nx, ny, pitch as for wcns_init;
- *           lo/hi/bc are ignored).  nvar > 4 returns WCNS_ERR_ARG.
+ *   grid:   layout of a and b: 1 <= nvar <= 4; ndim, dtype, reserved, nx, ny and pitch
+ *           obey the layout rules of wcns_init (ndim = 1 with ny > 1 is ny independent
+ *           lines, reduced over all of their cells); lo/hi/bc are ignored.  Any other
+ *           descriptor, nvar > 4 included, returns WCNS_ERR_ARG.
  *   a, b:   device grid buffers (b may be NULL: |a|); 16-byte aligned.
  *   what:   WCNS_REDUCE_SUM, _L1 or _LINF (else WCNS_ERR_UNSUPPORTED).
  *   stream: cudaStream_t the work is enqueued on (NULL: default stream).
  *   out:    DEVICE buffer of nvar doubles owned by the caller; written asynchronously.
- * The first call on a device resolves the array's device address (a CUDA runtime
- * query) with that device current; make that first call before any stream capture.
+ * The first call in a CUDA context (with the device current) resolves the array's
+ * device address (a CUDA runtime query) and caches it for that context; make that
+ * first call before any stream capture.  A device reset, or another context made
+ * current on the device, starts a new context, whose first call repeats the lookup.
  * All calls share the array and it keeps the last call's contents: each call clears
  * the counters it needs on its own stream.  Calls that overlap on the GPU (unordered
- * streams) race on the array and give wrong results. */
+ * streams) race on the array and give wrong results.  Safe to call from several host
+ * threads (the address cache is locked); their GPU work must still not overlap. */
 wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void* b, int32_t what,
                                 void* stream, double* out);
 

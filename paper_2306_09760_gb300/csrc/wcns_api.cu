@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/wcns.h"
+#include "wcns_grid_check.h"
 #include "wcns_internal.h"
 
 using namespace wcns;
@@ -374,16 +375,8 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   *out = nullptr;
   if (!grid || !params) return WCNS_ERR_ARG;
   const wcns_grid& g = *grid;
-  if (g.ndim != 1 && g.ndim != 2) return WCNS_ERR_ARG;
   if (g.nvar != 1 && g.nvar != 3 && g.nvar != 4) return WCNS_ERR_ARG;
-  if (g.dtype != WCNS_F64 && g.dtype != WCNS_F32) return WCNS_ERR_ARG;
-  if (g.reserved != 0) return WCNS_ERR_ARG;
-  const int64_t kMaxN = (int64_t)1 << 26;
-  if (g.nx < 1 || g.ny < 1 || g.nx > kMaxN || g.ny > kMaxN) return WCNS_ERR_ARG;
-  // ndim 1 with ny > 1: ny independent lines of nx cells (rows are not coupled)
-  if (g.ny > 65535 * (int64_t)43 || (g.ndim == 1 && g.ny > 65535)) return WCNS_ERR_ARG;
-  if (g.pitch < g.nx || g.pitch % 32 != 0) return WCNS_ERR_ARG;
-  if ((double)g.nvar * (double)g.ny * (double)g.pitch > 4.0e9) return WCNS_ERR_ARG;
+  if (check_grid_layout(g) != WCNS_OK) return WCNS_ERR_ARG;
   for (int d = 0; d < g.ndim; ++d) {
     if (!(g.hi[d] > g.lo[d])) return WCNS_ERR_ARG;
     if (g.bc[d] != WCNS_BC_PERIODIC && g.bc[d] != WCNS_BC_TRANSMISSIVE) return WCNS_ERR_ARG;
