@@ -1,18 +1,30 @@
-"""Shared FP64 parity criterion of the GPU tests.
+"""Shared parity criteria of the GPU tests.
 
-The GPU and the oracle round differently (FMA contraction, factored eigenvector
+FP64.  The GPU and the oracle round differently (FMA contraction, factored eigenvector
 products, CUDA's tanh/sqrt), so they agree to the last bits only where the scheme is
-well conditioned.  Two places are not: (1) long shocked runs, where the nonlinear
-weights amplify round-off step after step; (2) stretches of exactly constant data
-next to a jump, where IS ~ 1e-33 from round-off dwarfs eps = 1e-40 and so decides the
-Z weights.  The criterion is therefore: relative max error below 1e-11, or below ten
-times the oracle's own change when every input value moves by one ulp (the
-round-off amplification any correct implementation must be allowed).  The
-sensitivity is computed only when the strict bound is missed.
+well conditioned.  A single evaluation of L(u) on the initial data has no room for
+amplification: it must agree to 1e-11 relative max error outright (`strict=True`).
+Runs of many steps are another matter: the nonlinear weights amplify round-off step
+after step (and, on exactly constant stretches next to a jump, IS ~ 1e-33 from
+round-off dwarfs eps = 1e-40 and decides the Z weights).  For those the criterion is
+relative max error below 1e-11, or below ten times the oracle's own change when every
+input value moves by one ulp (the amplification any correct implementation must be
+allowed).  The sensitivity is computed only when the strict bound is missed, and every
+test that takes this allowance is recorded in FALLBACKS and listed at the end of the
+pytest run.
+
+FP32.  Relative L1 per conserved variable, mean |u32 - u64| / mean |u64| against the
+oracle: at most 1e-5 on smooth data and 1e-3 on shocked data (states after steps); a
+per-element bound beside it catches a misplaced cell or ghost that a mean would hide.
 """
 import numpy as np
 
 TOL64 = 1e-11
+L1_SMOOTH = 1e-5
+L1_SHOCKED = 1e-3
+
+# (what, GPU error, oracle one-ulp sensitivity) of every check that needed the allowance
+FALLBACKS = []
 
 
 def rel_max(a, b):
@@ -24,11 +36,25 @@ def perturb_ulp(u0, seed=0):
     return u0 * (1.0 + rng.choice([-1.0, 1.0], size=u0.shape) * 2.0 ** -52)
 
 
-def check64(got, ref, run_oracle, u0, what=""):
-    """run_oracle(u0) -> oracle result for input u0 (the unperturbed one gives ref)."""
+def allow_sensitivity(err, sens, what):
+    """The multi-step allowance: err < 10 x the oracle's one-ulp sensitivity, recorded."""
+    FALLBACKS.append((what, float(err), float(sens)))
+    assert err < 10.0 * sens, f"{what}: GPU vs oracle {err:.3e}, oracle 1-ulp sensitivity {sens:.3e}"
+    return err
+
+
+def check64(got, ref, run_oracle, u0, what="", strict=False):
+    """run_oracle(u0) -> oracle result for input u0 (the unperturbed one gives ref).
+    strict: a single evaluation, held to TOL64 with no allowance."""
     err = rel_max(got, ref)
     if err < TOL64:
         return err
+    assert not strict, f"{what}: GPU vs oracle {err:.3e} >= {TOL64} (single evaluation, no allowance)"
     sens = rel_max(run_oracle(perturb_ulp(u0)), ref)
-    assert err < 10.0 * sens, f"{what}: GPU vs oracle {err:.3e}, oracle 1-ulp sensitivity {sens:.3e}"
-    return err
+    return allow_sensitivity(err, sens, what)
+
+
+def rel_l1(u32, ref):
+    """Relative L1 per conserved variable (leading axis): mean |u32 - ref| / mean |ref|."""
+    axes = tuple(range(1, ref.ndim))
+    return np.abs(u32 - ref).mean(axis=axes) / np.maximum(np.abs(ref).mean(axis=axes), 1e-300)

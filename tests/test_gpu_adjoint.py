@@ -135,7 +135,8 @@ def test_rollout_gradient_matches_oracle_tangent(W):
         for seed in range(3):
             _, Jv_p = oracle.step_jvp(P, perturb_ulp(P.u0, seed), v, dt, steps, **params)
             sens = max(sens, abs(float(np.sum(w * Jv_p)) - lhs) / (np.linalg.norm(w) * np.linalg.norm(Jv)))
-        assert err < 10 * sens, (lhs, rhs, err, sens)
+        from parity import allow_sensitivity
+        allow_sensitivity(err, sens, "vortex rollout gradient, 8 steps")
 
 
 def test_gradient_matches_finite_differences_fp64(W):
@@ -216,3 +217,154 @@ def test_adjoint_configuration_gradient_matches_finite_differences(W):
             errs.append(abs(ad - fd) / abs(fd))
     S.close()
     assert min(errs) < 1e-6, (ad, errs)
+
+
+# ---------------------------------------------------------------------------
+# Single precision: the precision of the adjoint workload
+# ---------------------------------------------------------------------------
+# Bounds (relative to the product of norms, or to the FP64 norm).  The reverse sweep of
+# one RK3 step chains O(10^2) rounded operations per cotangent entry, so at the FP32
+# unit round-off 2^-24 = 6e-8 each step contributes a few 1e-6, and independent
+# rounding errors grow with the square root of the step count.  Measured on GB300:
+# 1.1e-5 for two steps (dot product), 1.5e-5 for 50 reverse steps; the bounds are ten
+# times the estimate.  Data whose weights are decided by round-off (exactly constant
+# stretches next to variation, eps far below IS) are ill conditioned in FP32 as in FP64
+# and are left to the FP64 tests; the single-precision cases use the adjoint
+# workload's eps = 1e-4 where the data are nearly constant.
+ADJ32_DOT = 1e-4        # dot product against the FP64 oracle tangent, two steps
+ADJ32_SWEEP = 1e-4      # FP32 against FP64 reverse sweep from the same checkpoints, 50 steps
+FP32_CASES = [
+    CASES[0],
+    ("vortex_char_fe_p2_eps1e-4", lambda: inputs.vortex(48, seed=4), dict(characteristic=True, zp=2, eps=1e-4)),
+    ("smooth2d_char_js_eps1e-12", lambda: inputs.random_smooth_euler_2d(36, 40, seed=2),
+     dict(characteristic=True, weights="JS", eps=1e-12)),
+    CASES[6],
+    CASES[7],
+]
+
+
+@pytest.mark.parametrize("name,make,extra", FP32_CASES, ids=[c[0] for c in FP32_CASES])
+def test_adjoint_dot_product_fp32(W, name, make, extra):
+    """<w, J v> from the oracle's FP64 forward tangent against <J^T w, v> from the FP32
+    adjoint (FP32 forward checkpoints, FP32 reverse sweep), two TVD-RK3 steps."""
+    P = make()
+    params = dict(flux="LLF_FROZEN", alpha=(3.0, 3.0), xi=100.0)
+    params.update(extra)
+    dt = 0.2 * min(P.h[0], P.h[1] if P.ndim == 2 else 1.0)
+    rng = np.random.default_rng(11)
+    errs = []
+    for trial in range(2):
+        v = rng.normal(size=P.u0.shape)
+        w = rng.normal(size=P.u0.shape)
+        _, Jv = oracle.step_jvp(P, P.u0, v, dt, 2, **params)
+        JTw = adjoint_of_steps(W, P, dt, 2, w, dtype="f32", **params)
+        lhs = float(np.sum(w * Jv))
+        rhs = float(np.sum(JTw * v))
+        errs.append(abs(lhs - rhs) / (np.linalg.norm(w) * np.linalg.norm(Jv)))
+    print(f"\nFP32 adjoint dot product {name}: " + ", ".join(f"{e:.2e}" for e in errs))
+    assert max(errs) < ADJ32_DOT, (name, errs)
+
+
+def _c5_setup(n):
+    """The adjoint workload's setup (vortex with 1 % density noise, frozen LLF at the
+    initial maximum wave speed, constant CFL-0.5 dt, FE at xi = 100, p = 2,
+    characteristic projection, eps = 1e-4) on an n x n grid."""
+    P = inputs.vortex(n, seed=0)
+    uu, vv, pp = P.extra["u"], P.extra["v"], P.extra["p"]
+    c = np.sqrt(1.4 * pp / P.extra["rho0"])
+    amax = float(max((np.abs(uu) + c).max(), (np.abs(vv) + c).max()))
+    dt = 0.5 * P.h[0] / amax
+    params = dict(flux="LLF_FROZEN", alpha=(amax, amax), xi=100.0, zp=2, characteristic=True, eps=1e-4)
+    return P, dt, params
+
+
+def test_fp32_reverse_sweep_matches_fp64(W):
+    """The FP32 reverse sweeps alone: from the same checkpoints (the FP64 forward rounded
+    to FP32) and the same seed, 50 FP32 adjoint steps agree with 50 FP64 adjoint steps
+    (oracle-checked above) to ADJ32_SWEEP in relative L2."""
+    import torch
+    P, dt, params = _c5_setup(128)
+    steps = 50
+    rng = np.random.default_rng(5)
+    seed = rng.normal(size=P.u0.shape)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S64 = W.Solver(P, "f64", stream=stream, **params)
+        S32 = W.Solver(P, "f32", stream=stream, **params)
+        ck64, ck32 = [], []
+        for _ in range(steps):
+            ck64.append(S64.u.clone())
+            ck32.append(S64.u.to(torch.float32))
+            S64.step(dt, 1)
+        lam64 = S64.set_state(seed, S64.alloc())
+        lam32 = S32.set_state(seed, S32.alloc())
+        for a, b in zip(reversed(ck64), reversed(ck32)):
+            W.wcns_adjoint_step(S64.ctx, a, dt, lam64, lam64)
+            W.wcns_adjoint_step(S32.ctx, b, dt, lam32, lam32)
+        g64, g32 = S64.numpy(lam64), S32.numpy(lam32)
+        st64, _ = S64.status()
+        st32, _ = S32.status()
+        S64.close()
+        S32.close()
+    assert st64 == W.WCNS_OK and st32 == W.WCNS_OK
+    err = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    comp = [float(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k])) for k in range(4)]
+    print(f"\nFP32 vs FP64 reverse sweep, 128^2, {steps} steps: {err:.2e} (per variable {comp})")
+    assert err < ADJ32_SWEEP, (err, comp)
+
+
+def test_fp32_gradient_of_the_adjoint_workload(W):
+    """The adjoint workload's objective at 128^2 and 50 steps, gradient in FP32 (FP32
+    forward with checkpoints, FP32 reverse sweeps) through torch.autograd:
+      * its directional derivative agrees with a fourth-order central difference of the
+        FP64 forward, and the FP32 gradient agrees with the FP64 gradient, each within
+        10 x the FP32 forward's own error level plus ADJ32_SWEEP -- the error level being
+        |rho32(T) - rho64(T)| / |rho64(T) - rho*| (the gradient is the adjoint of the
+        residual rho(T) - rho*, so the forward's rounding enters it at that ratio)."""
+    import torch
+    from paper_2306_09760_gb300 import autograd as wag
+    n, steps = 128, 50
+    P, dt, params = _c5_setup(n)
+    h = P.h[0]
+    rstar64 = torch.as_tensor(inputs.vortex_primitive(n, t=steps * dt)[0], device="cuda")
+    res = {}
+    for prec, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        U = torch.as_tensor(P.extra["u"], device="cuda", dtype=tdt)
+        V = torch.as_tensor(P.extra["v"], device="cuda", dtype=tdt)
+        pr = torch.as_tensor(P.extra["p"], device="cuda", dtype=tdt)
+        rstar = rstar64.to(tdt)
+        S = W.Solver(P, prec, stream=torch.cuda.Stream(), **params)
+
+        def fwd(rho0, S=S, U=U, V=V, pr=pr):
+            E = pr / 0.4 + 0.5 * rho0 * (U * U + V * V)
+            return wag.rollout(torch.stack([rho0, rho0 * U, rho0 * V, E]), S, dt, steps)
+
+        def J(rho0, fwd=fwd, rstar=rstar):
+            return 0.5 * h * h * torch.sum((fwd(rho0)[0] - rstar) ** 2)
+
+        rho0 = torch.as_tensor(P.extra["rho0"], device="cuda", dtype=tdt).clone().requires_grad_(True)
+        (g,) = torch.autograd.grad(J(rho0), rho0)
+        with torch.no_grad():
+            rhoT = fwd(rho0.detach())[0].double()
+        res[prec] = dict(S=S, J=J, rho0=rho0, g=g.double(), rhoT=rhoT)
+    fwd_level = float(torch.linalg.norm(res["f32"]["rhoT"] - res["f64"]["rhoT"]) /
+                      torch.linalg.norm(res["f64"]["rhoT"] - rstar64))
+    bound = 10.0 * fwd_level + ADJ32_SWEEP
+    g32, g64 = res["f32"]["g"], res["f64"]["g"]
+    grad_err = float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64))
+    dirn = torch.as_tensor(np.random.default_rng(4).normal(size=(n, n)), device="cuda")
+    ad32 = float(torch.sum(g32 * dirn))
+    J64, r64 = res["f64"]["J"], res["f64"]["rho0"]
+    fd_errs = []
+    with torch.no_grad():
+        f = lambda e: float(J64(r64.detach() + e * dirn))
+        for eps in (1e-5, 1e-6, 1e-7):
+            fd = (-f(2 * eps) + 8 * f(eps) - 8 * f(-eps) + f(-2 * eps)) / (12 * eps)
+            fd_errs.append(abs(ad32 - fd) / abs(fd))
+    for r in res.values():
+        r["S"].close()
+    print(f"\nFP32 gradient, 128^2 x {steps}: forward error level {fwd_level:.2e}, |g32 - g64|/|g64| "
+          f"{grad_err:.2e}, directional derivative vs FP64 central differences {min(fd_errs):.2e} "
+          f"(bound {bound:.2e})")
+    assert grad_err < bound, (grad_err, fwd_level)
+    assert min(fd_errs) < bound, (fd_errs, fwd_level)

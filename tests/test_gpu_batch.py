@@ -90,7 +90,9 @@ def test_batch_t_end_clipping(W):
         assert tref == 0.01
         sens = np.abs(refp - ref).max() / np.abs(ref).max()
         err = np.abs(out[:, o:o + n] - ref).max() / np.abs(ref).max()
-        assert err < max(1e-11, 10 * sens), (k, err, sens)
+        if err >= 1e-11:
+            from parity import allow_sensitivity
+            allow_sensitivity(err, sens, f"batch problem {k} to t=0.01")
 
 
 def test_batch_f32_l1(W):

@@ -47,7 +47,7 @@ def test_lines_shorter_than_the_stencil(W, n, bc, family):
     P = euler1d(n, seed=n, bc=bc)
     L = gpu_rhs(W, P, "f64", family=family)
     Lr, _ = oracle.rhs(P, family=family)
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family)[0], P.u0, f"n={n} bc={bc}")
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family)[0], P.u0, f"n={n} bc={bc}", strict=True)
     L32 = gpu_rhs(W, P, "f32", family=family)
     scale = max(np.abs(Lr).mean(), 1e-30)
     assert np.abs(L32 - Lr).mean() / scale < 1e-4 or np.abs(L32 - Lr).max() < 1e-5 * np.abs(P.u0).max()
@@ -60,7 +60,7 @@ def test_advection_tiny(W, n):
                        np.sin(np.pi * x)[None, None, :].copy() + 0.3, 0, adv_speed=(1.0, 0.0))
     L = gpu_rhs(W, P, "f64")
     Lr, _ = oracle.rhs(P)
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"adv n={n}")
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"adv n={n}", strict=True)
 
 
 @pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (1, 9), (9, 1), (260, 1), (1, 260)])
@@ -69,7 +69,7 @@ def test_thin_2d_grids(W, nx, ny):
     P = inputs.Problem("thin", 2, 4, nx, ny, (0.0, 0.0), (1.0, 1.0), (1, 0), Q.u0[:, :ny, :nx].copy(), 1)
     L = gpu_rhs(W, P, "f64")
     Lr, _ = oracle.rhs(P)
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{nx}x{ny}")
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{nx}x{ny}", strict=True)
 
 
 # 1224 rows give at least two waves of four-interface x blocks (1019-cell tiles) on a
@@ -103,7 +103,7 @@ def test_many_independent_lines(W):
     for j in (0, 1, 250, ny - 1):
         Q = inputs.Problem("line", 1, 3, nx, 1, (0.0, 0.0), (1.0, 1.0), (1, 1), u0[:, j:j + 1, :].copy(), 1)
         Lr, _ = oracle.rhs(Q)
-        check64(L[:, j:j + 1, :], Lr, lambda v: oracle.rhs(Q, v)[0], Q.u0, f"line {j}")
+        check64(L[:, j:j + 1, :], Lr, lambda v: oracle.rhs(Q, v)[0], Q.u0, f"line {j}", strict=True)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -125,12 +125,11 @@ def test_four_million_cell_line(W, dtype):
     got = L[:, 0, cells].T
     if dtype == "f64":
         err = np.abs(got - ref).max() / np.abs(ref).max()
-        if err >= 1e-11:
-            from parity import perturb_ulp
-            sens = np.abs(oracle.rhs_cells(P, perturb_ulp(P.u0), cells) - ref).max() / np.abs(ref).max()
-            assert err < 10 * sens, (err, sens)
+        assert err < 1e-11, err  # one evaluation: no round-off allowance
     else:
-        assert np.abs(got - ref).mean() / np.abs(ref).mean() < 1e-4
+        err = np.abs(got - ref)
+        assert err.mean() / np.abs(ref).mean() < 1e-4
+        assert err.max() < 3e-3 * np.abs(ref).max(), (err.max(), cells[err.max(axis=1).argmax()])
 
 
 def _line_sizes(kind):
@@ -168,7 +167,7 @@ def test_x_block_width_choice(W, kind, system, bc):
                            adv_speed=(1.0, 0.0))
     Lr, _ = oracle.rhs(P)
     L = gpu_rhs(W, P, "f64")
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{system} n={n} bc={bc}")
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{system} n={n} bc={bc}", strict=True)
     L32 = gpu_rhs(W, P, "f32")
     assert np.all(np.isfinite(L32))
     assert np.abs(L32 - Lr).mean() / np.abs(Lr).mean() < 1e-4, np.abs(L32 - Lr).mean() / np.abs(Lr).mean()

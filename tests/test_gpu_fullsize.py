@@ -60,13 +60,12 @@ def test_fullsize_rhs_sampled(W, problem, dtype):
     ref = oracle.rhs_cells(P, P.u0, jj * N + ii)
     if dtype == "f64":
         err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
-        if err >= 1e-11:
-            from parity import perturb_ulp
-            sens = np.max(np.abs(oracle.rhs_cells(P, perturb_ulp(P.u0), jj * N + ii) - ref)) / np.max(np.abs(ref))
-            assert err < 10 * sens, (err, sens)
+        assert err < 1e-11, err  # one evaluation: no round-off allowance
     else:
-        err = np.abs(got - ref).mean() / np.abs(ref).mean()
-        assert err < 1e-4, err
+        err = np.abs(got - ref)
+        assert err.mean() / np.abs(ref).mean() < 1e-4, err.mean() / np.abs(ref).mean()
+        # a misplaced cell or ghost would show as an O(|L|) error at one sampled cell
+        assert err.max() < 3e-3 * np.abs(ref).max(), (err.max(), err.max(axis=1).argmax())
 
 
 def test_fullsize_step_sampled(W, problem):
@@ -93,3 +92,44 @@ def test_fullsize_step_sampled(W, problem):
         ref[s] = u[:, 15, 15]
     err = np.max(np.abs(got - ref)) / np.max(np.abs(P.u0))
     assert err < 1e-11, err
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_fullsize_step_sampled_f32(W, problem, nsteps):
+    """FP32 TVD-RK3 steps at 2048^2 in the benchmark's launch configuration (four-interface
+    x tiles of 1019 cells, the compile-time default-scheme kernels, the fused y-sweep
+    stage epilogue), sampled cells against the oracle stepping the patch each cell
+    depends on (radius 15 per step): relative L1 per variable <= 1e-3 (shocked data) and
+    a per-element bound of 1e-5 of max|u0| that an error at a misplaced cell or ghost
+    would break."""
+    import torch
+    from parity import L1_SHOCKED, rel_l1
+    P = problem
+    wx, wy = oracle.max_wave(P)
+    dt = 0.5 / (wx / P.h[0] + wy / P.h[1])
+    R = 15 * nsteps
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f32", stream=stream)
+        S.step(dt, nsteps)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(10 + nsteps)
+        ii, jj = sample_cells(N, rng, 150, margin=R + 1)
+        got = S.u[:, torch.as_tensor(jj, device="cuda"), torch.as_tensor(ii, device="cuda")].double().cpu().numpy().T
+        st, _ = S.status()
+        S.close()
+    assert st == W.WCNS_OK
+    ref = np.zeros_like(got)
+    for s, (i, j) in enumerate(zip(ii, jj)):
+        patch = P.u0[:, j - R:j + R + 1, i - R:i + R + 1].copy()
+        Q = inputs.Problem("patch", 2, 4, 2 * R + 1, 2 * R + 1, (0.0, 0.0),
+                           ((2 * R + 1) * P.h[0], (2 * R + 1) * P.h[1]), (1, 1), patch, 1)
+        u, _, _, _ = oracle.step(Q, dt=dt, nsteps=nsteps)
+        ref[s] = u[:, R, R]
+    l1 = rel_l1(got.T, ref.T)
+    emax = np.abs(got - ref).max(axis=0) / np.abs(P.u0).max(axis=(1, 2))
+    print(f"\nFP32 2048^2 {nsteps} step(s), sampled: relative L1 {[f'{x:.2e}' for x in l1]}, "
+          f"max / max|u0| {[f'{x:.2e}' for x in emax]}")
+    assert np.all(l1 < L1_SHOCKED), l1
+    # measured 2e-7 after three steps: one FP32 rounding per operation, no weight flips
+    assert np.all(emax < 1e-5), emax

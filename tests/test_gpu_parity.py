@@ -101,7 +101,7 @@ def test_rhs_parity_f64(W, stream, name, make, params):
     P = make()
     L, nonph = gpu_rhs(W, stream, P, "f64", **params)
     Lr, nonph_r = oracle.rhs(P, **params)
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0, **params)[0], P.u0, name)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, **params)[0], P.u0, name, strict=True)
     assert nonph == nonph_r
 
 
@@ -124,7 +124,7 @@ def test_option_matrix_rhs_parity(W, stream, weights, flux, characteristic):
     for Q in (P, P2):
         L, _ = gpu_rhs(W, stream, Q, "f64", **params)
         Lr, _ = oracle.rhs(Q, **params)
-        check64(L, Lr, lambda u0: oracle.rhs(Q, u0, **params)[0], Q.u0, Q.name)
+        check64(L, Lr, lambda u0: oracle.rhs(Q, u0, **params)[0], Q.u0, Q.name, strict=True)
 
 
 def test_zp2_and_pfe(W, stream):
@@ -135,7 +135,7 @@ def test_zp2_and_pfe(W, stream):
     for params in (dict(zp=2), dict(weights="PFE", cv=1e-2), dict(weights="PFE", cv=1e-3, xi=100.0)):
         L, _ = gpu_rhs(W, stream, P, "f64", **params)
         Lr, _ = oracle.rhs(P, **params)
-        check64(L, Lr, lambda u0: oracle.rhs(P, u0, **params)[0], P.u0, str(params))
+        check64(L, Lr, lambda u0: oracle.rhs(P, u0, **params)[0], P.u0, str(params), strict=True)
 
 
 def test_advection_c1_full_run(W, stream):
@@ -182,6 +182,42 @@ def test_2d_steps(W, stream):
     check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=20)[0], P.u0, "riemann2d 20 steps")
     u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=20)
     assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
+
+
+def test_riemann2d_256_100_steps(W, stream):
+    """The 2D workload's 100-step parity point at 256^2 (seed 0, CFL steps): FP64 under
+    the multi-step criterion, FP32 relative L1 per variable <= 1e-3 (shocked)."""
+    from parity import L1_SHOCKED, rel_l1
+    P = inputs.riemann2d(256, seed=0)
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=100)
+    ur, tr, takenr, _ = oracle.step(P, nsteps=100)
+    assert taken == takenr == 100
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=100)[0], P.u0, "riemann2d 256^2 100 steps")
+    u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=100)
+    assert np.all(rel_l1(u32, ur) < L1_SHOCKED), rel_l1(u32, ur)
+
+
+def test_titarev_toro_steps(W, stream):
+    """Titarev-Toro (Sec. 4.2.2, Eq. 36), N = 2001, 300 CFL steps: FP64 under the
+    multi-step criterion, FP32 relative L1 <= 1e-3."""
+    from parity import L1_SHOCKED, rel_l1
+    P = inputs.titarev_toro(2001)
+    u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=300)
+    ur, tr, takenr, _ = oracle.step(P, nsteps=300)
+    assert taken == takenr == 300 and abs(t - tr) <= 1e-11 * tr
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=300)[0], P.u0, "titarev-toro 300 steps")
+    u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=300)
+    assert np.all(rel_l1(u32, ur) < L1_SHOCKED), rel_l1(u32, ur)
+
+
+def test_lax_steps(W, stream):
+    """Lax tube (Sec. 4.2.1, Eq. 34), N = 1000, 200 CFL steps with each flux."""
+    P = inputs.lax(1000)
+    for flux in ("HLLC", "ROE", "LLF"):
+        u, _, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=200, flux=flux)
+        ur, _, takenr, _ = oracle.step(P, nsteps=200, flux=flux)
+        assert taken == takenr == 200
+        check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=200, flux=flux)[0], P.u0, f"lax {flux} 200 steps")
 
 
 def test_2d_smooth_f32_l1(W, stream):
@@ -316,7 +352,9 @@ def test_parity_growth_curve(W, stream, case):
         us, _, _, _ = oracle.step(P, perturb_ulp(P.u0), nsteps=n, t_end=t_end)
         err, sens = rmax(u, ur), rmax(us, ur)
         curve.append((taken, err, sens))
-        assert err < 1e-11 or err < 10 * sens, (taken, err, sens)
+        if err >= 1e-11:
+            from parity import allow_sensitivity
+            allow_sensitivity(err, sens, f"{case} after {taken} steps")
         # the CFL steps follow the state, so the time carries the same amplification
         assert taken == takenr and abs(t - tr) <= max(1e-11, 10 * sens) * tr, (t, tr, sens)
     print(f"\nparity growth {case}: " + ", ".join(f"step {k}: {e:.2e} (oracle 1-ulp {s:.2e})" for k, e, s in curve))
