@@ -269,6 +269,87 @@ def time_solver(W, torch, S, stream, steps, warmup, profile=True):
     return ms, prof
 
 
+def measure_line(W, torch, inputs, dtype, steps, warmup, local, barrier, e2e_steps=10):
+    """Device-resident timing of `steps` RK3 steps of the 2048^2 workload in `dtype`,
+    per-kernel event times, clocks during the timed region, and the end-to-end rate
+    through wcns_step_host on a pinned host buffer (copies inside the timed region)."""
+    P = inputs.riemann2d(N_MAIN, seed=SEED)
+    tdtype = torch.float32 if dtype == "f32" else torch.float64
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream)
+        S.step(0.0, warmup)
+        torch.cuda.synchronize()
+        W.wcns_profile_enable(S.ctx, True)
+        W.wcns_profile_read(S.ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            S.step(0.0, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        ms = e0.elapsed_time(e1)
+        prof = W.wcns_profile_read(S.ctx)
+        W.wcns_profile_enable(S.ctx, False)
+        st, nonph = S.status()
+        if st != W.WCNS_OK:
+            raise RuntimeError(f"device status after the timed region: {W.wcns_status_string(st)}")
+        t_sim, steps_taken = S.time()
+
+        # e2e: the public host-buffer entry point, copies inside the timed region
+        host = torch.zeros((S.grid.nvar, S.grid.ny, S.grid.pitch), dtype=tdtype).pin_memory()
+        host[:, :, :P.nx] = torch.from_numpy(P.u0).to(tdtype)
+        e2e_steps = max(1, min(steps, e2e_steps))
+        W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
+        e2e_wall = time.perf_counter() - t0
+        barrier()
+        grid = S.grid
+        S.close()
+    return dict(P=P, ms=ms, prof=prof, clocks=clk.summary(), nonph=nonph, t_sim=t_sim, steps_taken=steps_taken,
+                e2e_wall=e2e_wall, e2e_steps=e2e_steps, state_bytes=grid.nvar * grid.ny * grid.pitch * (4 if dtype == "f32" else 8))
+
+
+def roofline_of(prof, ncell, dtype, alu_peak, alu_src):
+    """Dominant kernel and its ALU roofline: algorithmic flops per launch / mean launch time."""
+    dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
+    launches, tot_ms = prof[dom]
+    per_dir = flops_per_cell_rhs() / 2.0
+    stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0}.get(dom, 0)
+    flops_per_launch = ncell * (per_dir + stage_extra)
+    achieved = flops_per_launch / (tot_ms / launches / 1e3) / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": ncu_traffic(dom) if dtype == "f32" else None,
+            "peak_source": alu_src, "flops_per_launch": flops_per_launch, "launch_ms": tot_ms / launches}
+
+
+def fp64_probe_tflops(torch, n=4096, reps=3):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, float64, n^3, 2 n^3
+    flop), best of `reps` after one warm-up, CUDA events."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -288,82 +369,38 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    P = inputs.riemann2d(N_MAIN, seed=SEED)
-    ncell = P.nx * P.ny
     dtype = args.dtype
-    tdtype = torch.float32 if dtype == "f32" else torch.float64
-    elem = 4 if dtype == "f32" else 8
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        S = W.Solver(P, dtype, stream=stream)
-        S.step(0.0, args.warmup)
-        torch.cuda.synchronize()
-        W.wcns_profile_enable(S.ctx, True)
-        W.wcns_profile_read(S.ctx)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            barrier()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            S.step(0.0, args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            barrier()
-        ms = e0.elapsed_time(e1)
-        prof = W.wcns_profile_read(S.ctx)
-        W.wcns_profile_enable(S.ctx, False)
-        st, nonph = S.status()
-        if st != W.WCNS_OK:
-            raise RuntimeError(f"device status after the timed region: {W.wcns_status_string(st)}")
-        t_sim, steps_taken = S.time()
-
-        # e2e: the public host-buffer entry point, copies inside the timed region
-        host = torch.zeros((S.grid.nvar, S.grid.ny, S.grid.pitch), dtype=tdtype).pin_memory()
-        host[:, :, :P.nx] = torch.from_numpy(P.u0).to(tdtype)
-        e2e_steps = max(1, min(args.steps, 10))
-        W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            W.wcns_step_host(S.ctx, host, 0.0, 1, 0.0)
-        e2e_wall = time.perf_counter() - t0
-        barrier()
-        S.close()
-
-    ms_max, e2e_max = max_over_ranks([ms, e2e_wall], world, device="cuda")
+    m = measure_line(W, torch, inputs, dtype, args.steps, args.warmup, local, barrier)
+    P = m["P"]
+    ncell = P.nx * P.ny
+    ms_max, e2e_max = max_over_ranks([m["ms"], m["e2e_wall"]], world, device="cuda")
     value = whole_job_rate(world, ncell, args.steps, ms_max / 1e3)
-    e2e_value = whole_job_rate(world, ncell, e2e_steps, e2e_max)
-    state_bytes = S.grid.nvar * S.grid.ny * S.grid.pitch * elem
+    e2e_value = whole_job_rate(world, ncell, m["e2e_steps"], e2e_max)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    # dominant kernel and its roofline (algorithmic flops per launch / event duration)
-    dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
-    launches, tot_ms = prof[dom]
-    flops_cell = flops_per_cell_rhs()
-    per_dir = flops_cell / 2.0
-    stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0}.get(dom, 0)
-    flops_per_launch = ncell * (per_dir + stage_extra)
-    achieved_tflops = flops_per_launch / (tot_ms / launches / 1e3) / 1e12
+    prof = m["prof"]
     hbm_peak, hbm_kind = measured_peaks()
     alg_gbs = value * 1e6 * ALG_BYTES_PER_CELL_UPDATE[dtype] / 1e9
-    alu_peak = FP32_ALU_PEAK_TFLOPS if dtype == "f32" else FP64_ALU_PEAK_TFLOPS
-    alu_src = ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if dtype == "f32"
-               else "nominal GB300 FP64 rate (a probe measured 1.20 TFLOP/s)")
-    traffic = ncu_traffic(dom) if dtype == "f32" else None
+    fp64_peak = fp64_probe_tflops(torch)
+    fp64_src = f"measured: cuBLAS DGEMM (torch.matmul float64 4096^3, best of 3) = {fp64_peak:.3f} TFLOP/s"
+    if dtype == "f32":
+        alu_peak, alu_src = FP32_ALU_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    else:
+        alu_peak, alu_src = fp64_peak, fp64_src
+    roof = roofline_of(prof, ncell, dtype, alu_peak, alu_src)
     gpu_launches = sum(v[0] for v in prof.values())
-
-    variants = {}
-    if not args.no_variants:
-        variants = run_variants(args, W, torch, inputs, hbm_peak)
 
     cpu = None
     if world == 1 and not args.no_cpu:
         cpu, _, _ = cpu_sample_rate(seconds_target=args.cpu_seconds, single_core_seconds=3.0)
+
+    variants = {}
+    if not args.no_variants:
+        variants = run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, barrier, cpu)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -374,18 +411,15 @@ def run_ours(args):
                                + ("FP32 bulk" if dtype == "f32" else "FP64"),
                    "global_batch": world, "seq_len": N_MAIN, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2: each stage touches 4 state-size arrays (256 MiB) > 126 MiB L2",
-                   "simulated_time": t_sim, "steps_taken": steps_taken, "fallback_interfaces": nonph},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_tflops, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": traffic,
-                     "peak_source": alu_src,
-                     "flops_per_launch": flops_per_launch, "launch_ms": tot_ms / launches},
+                   "simulated_time": m["t_sim"], "steps_taken": m["steps_taken"], "fallback_interfaces": m["nonph"]},
+        "roofline": roof,
         "hbm": {"achieved_gbs": alg_gbs, "peak_gbs": hbm_peak, "frac": alg_gbs / hbm_peak,
                 "peak_source": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE[dtype]},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},
-        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": m["state_bytes"],
+                "d2h_bytes_per_step": m["state_bytes"], "steps": m["e2e_steps"]},
+        "clocks": m["clocks"],
         "gpu_launches": gpu_launches,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]},
         "variants": variants,
@@ -396,12 +430,44 @@ def run_ours(args):
     return 0
 
 
-def run_variants(args, W, torch, inputs, hbm_peak):
-    """Secondary workloads of the same metric (short runs)."""
+def run_f64_line(W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, barrier, cpu, steps=20, warmup=3):
+    """The same workload at the paper's precision (FP64 throughout) as a full record:
+    device-resident rate, roofline of the dominant kernel against the measured FP64 rate,
+    HBM fraction, end to end through wcns_step_host, clocks, launches."""
+    m = measure_line(W, torch, inputs, "f64", steps, warmup, local, barrier, e2e_steps=5)
+    ncell = m["P"].nx * m["P"].ny
+    value = ncell * steps / (m["ms"] / 1e3) / 1e6
+    alg_gbs = value * 1e6 * ALG_BYTES_PER_CELL_UPDATE["f64"] / 1e9
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": m["ms"] / steps, "dtype": "f64",
+        "config": {"workload": "2D Euler 2048x2048, four-quadrant Riemann data (seed 0), transmissive, CFL 0.5, "
+                               "WCNS-FE (xi=1e6, kappa=0.5), HLLC, characteristic; FP64 throughout",
+                   "simulated_time": m["t_sim"], "steps_taken": m["steps_taken"]},
+        "roofline": roofline_of(m["prof"], ncell, "f64", fp64_peak, fp64_src),
+        "roofline_nominal_frac": roofline_of(m["prof"], ncell, "f64", FP64_ALU_PEAK_TFLOPS, "nominal")["frac"],
+        "hbm": {"achieved_gbs": alg_gbs, "peak_gbs": hbm_peak, "frac": alg_gbs / hbm_peak,
+                "bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE["f64"]},
+        "e2e": {"value": ncell * m["e2e_steps"] / m["e2e_wall"] / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": m["state_bytes"], "d2h_bytes_per_step": m["state_bytes"],
+                "steps": m["e2e_steps"]},
+        "clocks": m["clocks"],
+        "gpu_launches": sum(v[0] for v in m["prof"].values()),
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in m["prof"].items() if v[0]},
+        "cpu_baseline": cpu,
+    }
+
+
+def run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, barrier, cpu):
+    """Secondary workloads of the same metric (short runs), and the full FP64 record."""
     out = {}
     stream = torch.cuda.Stream()
+    try:
+        out["euler2d_2048_f64_full"] = run_f64_line(W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, barrier,
+                                                    cpu=cpu)
+    except Exception as e:  # reported, not hidden
+        out["euler2d_2048_f64_full"] = {"error": repr(e)}
     cases = [
-        ("euler2d_2048_f64", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f64", 2, 1, {}),
         ("sod_4096_f64", lambda: inputs.sod(4096), "f64", 200, 20, {}),
         ("sod_4096_f32", lambda: inputs.sod(4096), "f32", 200, 20, {}),
         ("shu_osher_4096_f64", lambda: inputs.shu_osher(4096), "f64", 200, 20, {}),
@@ -441,8 +507,10 @@ def run_variants(args, W, torch, inputs, hbm_peak):
 
 def run_fp32_error(W, torch, inputs):
     """Error of the FP32 bulk path per config: mean |u_f32 - u_f64| per component over the
-    mean |u_f64|, after the same run (the FP64 path matches the oracle to 1e-11 or its
-    round-off sensitivity, so it stands for it here)."""
+    mean |u_f64| against the FP64 GPU path after the same run (the timed program runs no
+    oracle code; the FP32-against-oracle figures of the same configurations are asserted
+    by tests/test_gpu_fp32_error.py, and the FP64 path matches the oracle to 1e-11 or its
+    round-off sensitivity)."""
     import numpy as np
     cases = [
         ("C1_advection_200_t2", lambda: inputs.advection_sine(200), 400, 0.0),
@@ -451,7 +519,7 @@ def run_fp32_error(W, torch, inputs):
         ("C3_riemann2d_512_100steps", lambda: inputs.riemann2d(512, seed=SEED), 100, 0.0),
         ("C5_vortex_512_200steps", lambda: inputs.vortex(512, seed=0), 200, 0.0),
     ]
-    out = {}
+    out = {"reference": "FP64 GPU path, same run", "measure": "relative L1 per conserved variable"}
     stream = torch.cuda.Stream()
     for name, make, nsteps, t_end in cases:
         P = make()
@@ -493,6 +561,10 @@ def run_batched_variant(W, torch, inputs, hbm_peak, steps=10):
     rate = total * steps / (ms / 1e3) / 1e6
     return {"value": rate, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "cells": total,
             "problems": len(sizes), "tile": tile, "blocks_per_sm": bps, "autotune_candidates": cands,
+            "config": "4096 1D Euler problems, N ~ U{64..8192} (seed 0), 1-4 piecewise-constant pieces with "
+                      "rho ~ U[0.5, 1.5], u ~ U[-0.5, 0.5], p ~ U[0.3, 1.5] (narrowed from the 2D quadrant "
+                      "ranges so no problem reaches a negative pressure), density x (1 + 0.1 sin 2 pi m x), "
+                      "transmissive, CFL 0.5, WCNS-FE (xi=1e6), HLLC, characteristic",
             "status": W.wcns_status_string(st), "hbm_frac": rate * 1e6 * 96 / 1e9 / hbm_peak}
 
 
@@ -527,7 +599,11 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
     h = P.h[0]
     T = steps * dt
     rstar_np = inputs.vortex_primitive(n, t=T)[0]
-    res = {"cells": n * n, "steps": steps, "dt": dt, "alpha": amax}
+    res = {"cells": n * n, "steps": steps, "dt": dt, "alpha": amax,
+           "config": "isentropic vortex (strength 5, mean flow (1, 1)) on periodic [0,10]^2, 512^2, 1% density "
+                     "noise (seed 0), 200 TVD-RK3 steps of constant dt (CFL 0.5 at t = 0), LLF with alpha frozen "
+                     "at the initial maximum wave speed, FE xi = 100, Z p = 2, characteristic, eps = 1e-4 (raised "
+                     "from 1e-40 so the 200-step tangent stays bounded), J = 1/2 h^2 sum (rho(T) - rho*)^2"}
 
     def make_J(S, tdt):
         U = torch.as_tensor(P.extra["u"], device="cuda", dtype=tdt)

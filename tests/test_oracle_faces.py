@@ -63,3 +63,41 @@ def test_dmr_shock_moves_at_the_exact_speed():
     front = x[np.argmax(rho_top < 0.5 * (8.0 + 1.4))]
     exact = 1.0 / 6.0 + (1.0 + 20.0 * 0.2) / np.sqrt(3.0)
     assert abs(front - exact) < 3 * (4.0 / 240), (front, exact)
+
+
+def test_eq3_difference_loses_positivity_at_the_dmr_shock():
+    """Why the double Mach reflection (Sec. 4.3) runs with the FE-WENO family: across the
+    Mach 10 shock (pressure ratio 116.5) the sixth-order midpoint difference of Eq. 3,
+    whose second and third coefficients reach two and three interfaces upstream with
+    d2 < 0, drives the second pre-shock cell to a negative pressure in the first RK
+    stage at CFL 0.5 -- with the very interface fluxes under which the two-point
+    difference of App. B keeps every cell physical.  (The 2D problem fails the same way
+    on every row at the shock front, not only next to the wall.)"""
+    g, n = 1.4, 400
+    x = inputs.cell_centres(0.0, 1.0, n)
+    post, pre = (8.0, 8.25, 116.5), (1.4, 0.0, 1.0)  # normal-shock states of the DMR
+    prim = [np.where(x < 0.3, a, b) for a, b in zip(post, pre)]
+    u0 = inputs.prim_to_cons(prim[0][None, :], prim[1][None, :], None, prim[2][None, :], g, 1)
+    U = u0[:, 0, :].T
+
+    def cell(k):
+        return U[min(max(k, 0), n - 1)]
+
+    # F[k + 3] = F_{k+1/2}, the WCNS-FE interface flux (characteristic FE, HLLC)
+    F = np.array([oracle.interface_flux(np.array([cell(k + m) for m in range(-2, 4)]), 3)[0]
+                  for k in range(-3, n + 2)])
+    h = 1.0 / n
+    dt = 0.5 * h / (8.25 + np.sqrt(g * 116.5 / 8.0))
+    d1, d2, d3 = 75 / 64, -25 / 384, 3 / 640
+    bad_eq3, bad_two_point = [], []
+    for i in range(n):
+        f = [F[i + 3 + m] for m in range(-3, 3)]  # F_{i-5/2} .. F_{i+5/2}
+        L3 = -(d1 * (f[3] - f[2]) + d2 * (f[4] - f[1]) + d3 * (f[5] - f[0])) / h
+        L2 = -(f[3] - f[2]) / h
+        for L, bad in ((L3, bad_eq3), (L2, bad_two_point)):
+            v = U[i] + dt * L
+            if not (v[0] > 0 and (g - 1) * (v[2] - 0.5 * v[1] ** 2 / v[0]) > 0):
+                bad.append(i)
+    first_pre = int(np.argmax(x >= 0.3))
+    assert bad_eq3 == [first_pre + 1]
+    assert bad_two_point == []
