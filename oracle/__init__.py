@@ -8,7 +8,9 @@ function follows.
 Parity status: every function is pinned by `tests/test_oracle_*.py` against values
 the paper prints (Table 1 and Table B.1 control values), closed forms (the linear scheme's Fourier
 symbol, polynomial exactness, Eq. 18 truncation coefficients, the exact Riemann
-solution), invariants (conservation, symmetry) and central finite differences.
+solution, the JS and M weights of Eq. 11-13 in exact rational arithmetic, the CFL
+step of uniform states and of the Sod tube), invariants (conservation, symmetry) and
+central finite differences.
 The weight statistics (`weight_hist`) are parity unpinned: the paper's Tables A.1-A.4
 depend on solver settings it does not state.
 """

@@ -68,6 +68,12 @@ struct SchemeT {
   int xi_small;  // single precision with xi < 1e4: the FE map uses the exponential form of tanh
   T gamma, gm1, eps, xi, cv, harten;
   T sat_dist;    // |w - null| at and beyond which every FE tanh term is saturated (kSat / xi)
+  // Ideal-plateau test of the FE map (weights == FE only; 0 = off): where every base weight
+  // w_k lies within ideal_margin[k] of the ideal weight d_k, it is farther than the
+  // saturation distance from every null point, inside the plateau whose control value is
+  // d_k, so Eq. 20 returns the ideal weights exactly; they sum to exactly 1, so the
+  // renormalised weights are the ideal weights, which the kernels then use directly.
+  T ideal_margin[3];
   T speed[2];
   T null0[3], null1[4], null2[3];
   T ideal[3], ctrl0[2], ctrl1[3], ctrl2[2];
@@ -111,6 +117,40 @@ inline Faces<T> faces_as(const Faces<double>& f) {
   return r;
 }
 
+// Margins of the ideal-plateau test (SchemeT::ideal_margin), from the null points of each
+// map: the distance from d_k to its nearest null point, less the saturation distance of
+// the saturated evaluation (with the single-precision test's own allowance in double
+// precision) and a rounding allowance.  Off (0) unless the weights are FE, the map is
+// evaluated in saturated form, d_k lies strictly inside the plateau whose control value
+// it is (true for both families at kappa = 0.5), and the ideal weights sum to exactly 1
+// in the kernel's precision.
+template <typename T>
+inline void ideal_margins(const Scheme& s, SchemeT<T>& r) {
+  for (int k = 0; k < 3; ++k) r.ideal_margin[k] = T(0);
+  if (s.weights != 2 || r.xi_small) return;
+  if (T(T(s.ideal[0]) + T(s.ideal[1])) + T(s.ideal[2]) != T(1)) return;
+  const double sat = (sizeof(T) == 4 ? 9.1 : 20.0 + 1.0e-4 + 4.0e-7 * s.xi) / s.xi;
+  const double* nulls[3] = {s.null0, s.null1, s.null2};
+  const int count[3] = {3, 4, 3};
+  const double ctrl0[3] = {s.ctrl0[0], s.ctrl1[0], s.ctrl2[0]};
+  double m[3];
+  for (int k = 0; k < 3; ++k) {
+    const double d = s.ideal[k];
+    if (ctrl0[k] != d) return;
+    double lo = -1.0, hi = 2.0;
+    for (int j = 0; j < count[k]; ++j) {
+      const double n = nulls[k][j];
+      if (n <= d && n > lo) lo = n;
+      if (n > d && n < hi) hi = n;
+    }
+    // d must lie between the first two null points (the plateau of control value d)
+    if (!(lo == nulls[k][0] && hi == nulls[k][1])) return;
+    m[k] = (d - lo < hi - d ? d - lo : hi - d) * (1.0 - 1.0e-6) - sat * (1.0 + 1.0e-3) - 1.0e-6;
+    if (!(m[k] > 0.0)) return;
+  }
+  for (int k = 0; k < 3; ++k) r.ideal_margin[k] = T(m[k]);
+}
+
 template <typename T>
 inline SchemeT<T> scheme_as(const Scheme& s) {
   SchemeT<T> r;
@@ -129,6 +169,7 @@ inline SchemeT<T> scheme_as(const Scheme& s) {
   for (int j = 0; j < 4; ++j) r.null1[j] = T(s.null1[j]);
   for (int k = 0; k < 3; ++k) { r.ideal[k] = T(s.ideal[k]); r.ctrl1[k] = T(s.ctrl1[k]); }
   for (int k = 0; k < 2; ++k) { r.ctrl0[k] = T(s.ctrl0[k]); r.ctrl2[k] = T(s.ctrl2[k]); }
+  ideal_margins<T>(s, r);
   return r;
 }
 
@@ -504,7 +545,11 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
     const T isa = Num<T>::rcp_(a0 + a1 + a2);
     w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
     if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
-    if (weights >= 2) {
+    if (weights == 2 && s.ideal_margin[0] > T(0) && Num<T>::abs_(w0 - d0) < s.ideal_margin[0] &&
+        Num<T>::abs_(w1 - d1) < s.ideal_margin[1] && Num<T>::abs_(w2 - d2) < s.ideal_margin[2]) {
+      // inside the ideal plateaus: Eq. 20 and the renormalisation give the ideal weights
+      w0 = d0; w1 = d1; w2 = d2;
+    } else if (weights >= 2) {
       bool keep = false;
       if (weights == 3) {
         // App. A: keep the Z weights inside the closed box |w_k - d_k| <= cv

@@ -129,6 +129,20 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
     const P2 a0 = fma(bc(d0), r0, bc(d0)), a1 = fma(bc(d1), r1, bc(d1)), a2 = fma(bc(d2), r2, bc(d2));
     const P2 isa = rcp(add(add(a0, a1), a2));
     w0 = mul(a0, isa); w1 = mul(a1, isa); w2 = mul(a2, isa);
+    if (weights == 2 && s.ideal_margin[0] > 0.0f) {
+      // both lanes inside the ideal plateaus of Eq. 20: the map gives the ideal weights,
+      // whose sum is exactly 1, so the renormalised weights are the ideal ones and Eq. 6
+      // takes them as they are (the staircase below reaches the same weights through its
+      // comparisons and a reciprocal of 1 from the reciprocal unit)
+      float a, b;
+      split(sub(w0, bc(d0)), a, b);
+      bool ideal = fmaxf(fabsf(a), fabsf(b)) < s.ideal_margin[0];
+      split(sub(w1, bc(d1)), a, b);
+      ideal = ideal && fmaxf(fabsf(a), fabsf(b)) < s.ideal_margin[1];
+      split(sub(w2, bc(d2)), a, b);
+      ideal = ideal && fmaxf(fabsf(a), fabsf(b)) < s.ideal_margin[2];
+      if (ideal) return fma(bc(d2), q2, fma(bc(d1), q1, mul(bc(d0), q0)));
+    }
     if (weights >= 2) {
       float l0, l1, l2, r0s, r1s, r2s;
       split(w0, l0, r0s); split(w1, l1, r1s); split(w2, l2, r2s);

@@ -70,7 +70,7 @@ def test_dmr_steps_parity_f64(W):
 
 def test_dmr_full_run_f64_f32(W):
     """To t = 0.2 on 240 x 60 (about 700 steps) with the FE-WENO family: FP64 under the
-    round-off criterion, FP32 in relative L1, and the top-row shock at its exact place."""
+    round-off criterion, FP32 in relative L1 (<= 1e-3), and the top-row shock at its exact place."""
     P = inputs.dmr(240, 60)
     u, t, _ = gpu_steps(W, P, "f64", 5000, t_end=0.2, family="WENO")
     ur, tr, _, _ = oracle.run_to(P, 0.2, family="WENO")
@@ -80,7 +80,7 @@ def test_dmr_full_run_f64_f32(W):
     assert abs(t32 - 0.2) < 1e-12
     rel = np.abs(u32 - ur).mean(axis=(1, 2)) / np.abs(ur).mean(axis=(1, 2))
     print(f"\nDMR 240 x 60 to t = 0.2, FP32 vs oracle relative L1 {[f'{x:.2e}' for x in rel]}")
-    assert np.all(rel < 5e-3), rel
+    assert np.all(rel < 1e-3), rel  # the shocked-data bound (measured 1.6e-4)
 
 
 @pytest.mark.parametrize("family", ["WCNS", "WENO"])
