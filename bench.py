@@ -114,12 +114,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_digest():
-    h = hashlib.sha256()
+# The sources of the sweep and CFL kernels' code: device numerics, the packed
+# single-precision interface flux, and the kernel bodies.
+SWEEP_SOURCES = ("wcns_device.cuh", "wcns_pair.cuh", "wcns_kernels.cuh")
+
+
+def kernel_source_digest(read=None):
+    """Digest of the sweep and CFL kernels' sources (read(name) -> bytes; default: the
+    working tree)."""
     d = os.path.join(ROOT, "paper_2306_09760_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode() + open(os.path.join(d, name), "rb").read())
+    read = read or (lambda name: open(os.path.join(d, name), "rb").read())
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        h.update(name.encode() + read(name))
     return h.hexdigest()[:16]
 
 
@@ -472,6 +479,9 @@ def run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, b
         ("sod_4096_f32", lambda: inputs.sod(4096), "f32", 200, 20, {}),
         ("shu_osher_4096_f64", lambda: inputs.shu_osher(4096), "f64", 200, 20, {}),
         ("euler2d_2048_f32_xi100", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f32", 10, 3, dict(xi=100.0)),
+        # data-dependence of the FE ideal-plateau path: smooth everywhere, and rough everywhere
+        ("euler2d_2048_f32_smooth", lambda: inputs.random_smooth_euler_2d(N_MAIN, N_MAIN, seed=1), "f32", 20, 3, {}),
+        ("euler2d_2048_f32_rough", lambda: inputs.rough_euler_2d(N_MAIN, N_MAIN, seed=1), "f32", 20, 3, {}),
         ("advection_200_f64", lambda: inputs.advection_sine(200), "f64", 400, 20, {}),
         ("euler2d_2048_f32_fe_weno", lambda: inputs.riemann2d(N_MAIN, seed=SEED), "f32", 10, 3,
          dict(family="WENO")),
@@ -497,11 +507,16 @@ def run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, b
         with torch.cuda.stream(stream):
             S = W.Solver(P, dt, stream=stream, **params)
             ms, prof = time_solver(W, torch, S, stream, steps, warm, profile=False)
+            st, _ = S.status()
+            _, taken = S.time()
             S.close()
         rate = P.nx * P.ny * steps / (ms / 1e3) / 1e6
         nbytes = ALG_BYTES_PER_CELL_UPDATE[dt] * P.nvar / 4 if P.nvar != 4 else ALG_BYTES_PER_CELL_UPDATE[dt]
-        out[name] = {"value": rate, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-                     "hbm_frac": rate * 1e6 * nbytes / 1e9 / hbm_peak}
+        # a run that froze (non-physical state: dt = 0) skipped work; its rate is not reported
+        ok = st == W.WCNS_OK and taken == steps + warm
+        out[name] = {"value": rate if ok else None, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                     "hbm_frac": rate * 1e6 * nbytes / 1e9 / hbm_peak if ok else None,
+                     "status": W.wcns_status_string(st), "steps_taken": taken}
     return out
 
 

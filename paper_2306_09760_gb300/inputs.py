@@ -299,6 +299,23 @@ def random_smooth_euler_2d(nx, ny, seed=0, periodic=True):
     return Problem(f"smooth2d_{seed}", 2, 4, nx, ny, (0.0, 0.0), (1.0, 1.0), bc, u0, 1)
 
 
+def rough_euler_2d(nx, ny, seed=0, amp=0.1):
+    """2D Euler data with no smooth or constant stretch anywhere: the smooth field of
+    random_smooth_euler_2d with an independent uniform perturbation of relative size amp
+    in every cell's density and pressure (seeded), periodic.  Throughput context for the
+    weight-dependent paths of the kernels (test and benchmark input)."""
+    P = random_smooth_euler_2d(nx, ny, seed=seed, periodic=True)
+    noise = np.random.default_rng(int(seed) * 7877 + 11).uniform(-amp, amp, size=(2, ny, nx))
+    rho0 = P.u0[0]
+    u = P.u0[1] / rho0
+    v = P.u0[2] / rho0
+    p = 0.4 * (P.u0[3] - 0.5 * rho0 * (u * u + v * v))
+    rho = rho0 * (1.0 + noise[0])
+    p = p * (1.0 + noise[1])
+    u0 = prim_to_cons(rho, u, v, p, 1.4, 2)
+    return Problem(f"rough2d_{seed}", 2, 4, nx, ny, (0.0, 0.0), (1.0, 1.0), (0, 0), u0, 1)
+
+
 def random_smooth_euler_1d(n, seed=0, periodic=True):
     """Smooth, positive 1D Euler data from a few random Fourier modes (test input)."""
     g = SplitMix64(int(seed) * 6007 + 9)
