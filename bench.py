@@ -603,6 +603,33 @@ def adjoint_problem(inputs, n=512, seed=0):
     return P, amax, dt
 
 
+def adjoint_kernel_times(W, torch, inputs, steps=20):
+    """Per-kernel CUDA-event times of `steps` FP32 adjoint steps of the adjoint workload
+    (library profiler): forward checkpoints first, then the reverse steps."""
+    import numpy as np
+    P, amax, dt = adjoint_problem(inputs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f32", stream=stream, alpha=(amax, amax), **ADJ_PARAMS)
+        ck = []
+        for _ in range(steps):
+            ck.append(S.u.clone())
+            S.step(dt, 1)
+        lam = S.set_state(np.random.default_rng(0).normal(size=P.u0.shape), S.alloc())
+        W.wcns_adjoint_step(S.ctx, ck[-1], dt, lam, lam)  # untimed: first-call allocations
+        torch.cuda.synchronize()
+        W.wcns_profile_enable(S.ctx, True)
+        W.wcns_profile_read(S.ctx)
+        for un in reversed(ck):
+            W.wcns_adjoint_step(S.ctx, un, dt, lam, lam)
+        prof = W.wcns_profile_read(S.ctx)
+        W.wcns_profile_enable(S.ctx, False)
+        st, _ = S.status()
+        S.close()
+    return {"steps": steps, "status": W.wcns_status_string(st),
+            "kernels": {k: {"launches": v[0], "ms": v[1], "ms_per_step": v[1] / steps} for k, v in prof.items() if v[0]}}
+
+
 def run_adjoint_variant(W, torch, inputs, steps=200):
     """C5: gradient of J = 1/2 h^2 sum (rho(T) - rho*)^2 w.r.t. the initial density through
     200 TVD-RK3 steps.  FP32 forward (with per-step checkpoints) and hand-written adjoint
@@ -664,6 +691,7 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
                                    "best_rel_err": min(fd_err.values())}
         S.close()
     res["f32_vs_f64_grad_rel"] = float(torch.linalg.norm(grads["f32"] - grads["f64"]) / torch.linalg.norm(grads["f64"]))
+    res["f32_adjoint_kernels"] = adjoint_kernel_times(W, torch, inputs)
     res["value"] = res["f32"]["adjoint_mcells"]
     res["unit"] = UNIT + " (adjoint, FP32)"
     return res
@@ -680,7 +708,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"],
                     help="element type of the main line (default f32: FP32 bulk arithmetic)")
+    ap.add_argument("--adjoint-kernels", type=int, default=0, metavar="STEPS",
+                    help="only time STEPS FP32 adjoint steps of the adjoint workload per kernel (for profiling)")
     args = ap.parse_args()
+    if args.adjoint_kernels > 0:
+        import torch
+        from paper_2306_09760_gb300 import build as wbuild, inputs, wcns as W
+        wbuild.build()
+        print(json.dumps(adjoint_kernel_times(W, torch, inputs, steps=args.adjoint_kernels)), flush=True)
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -156,7 +156,10 @@ wcns_status wcns_rhs(wcns_ctx* ctx, const void* u, void* dudt);
  * or, with integrator WCNS_RK4, classical RK4 steps written as in Eq. 16 (one more
  * stage state of scratch, allocated by wcns_init).
  * dt > 0: fixed step.  dt <= 0: each step takes dt = cfl / sum_d(max(|u_d| + c) / h_d)
- * (advection: |a_d| for max(|u_d| + c)), reduced on the device, never read back.
+ * (advection: |a_d| for max(|u_d| + c)), reduced on the device, never read back.  On
+ * 2D Euler grids the first step of a call reduces the maxima from u, and each step's
+ * last RK stage reduces them from the state it writes for the step after it (the same
+ * values, without a separate read of u).
  * t_end > 0: each step is clipped so the device time t never passes t_end; once t
  * reaches t_end further steps do nothing.  The device time starts at 0 (see
  * wcns_set_time) and is read with wcns_get_time.  Asynchronous. */
@@ -267,7 +270,7 @@ wcns_status wcns_profile_enable(wcns_ctx* ctx, int32_t on);
 
 /* Synchronises the stream and returns, per kernel kind, its name (48-byte slots in
  * `names`), launches and total milliseconds since the last read, then resets them.
- * max_entries must be >= 9 (the number of kinds); *n_entries receives that number. */
+ * max_entries must be >= 10 (the number of kinds); *n_entries receives that number. */
 wcns_status wcns_profile_read(wcns_ctx* ctx, int32_t max_entries, char* names, int64_t* launches,
                               double* ms, int32_t* n_entries);
 

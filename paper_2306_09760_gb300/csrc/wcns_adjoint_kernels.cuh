@@ -44,8 +44,17 @@ WCNS_HD T adj_combine(const AdjArgs<T>& A, int64_t off, int k, T jt, T mu) {
 template <typename T, int NV>
 constexpr size_t adj_x_smem() { return sizeof(T) * NV * (2 * kXCells + 6 * kXThreads); }
 
+// The x adjoint covers the forward tile (kXThreads interfaces, kXTile cells) with
+// kAXThreads threads, two interfaces each: on the 512^2 adjoint workload 128-thread
+// blocks (four resident per SM in single precision) ran 0.171 ms per launch against 0.214
+// for 256 threads with one interface each (the block waits on its slowest warp's reverse
+// sweep at the barrier) and 0.275 for 64 threads with four each.
+constexpr int kAXThreads = 128;
+template <typename T>
+constexpr int adj_x_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
+
 template <typename T, int NV, int MODE>
-__global__ void __launch_bounds__(kXThreads) adjoint_x_kernel(AdjArgs<T> A) {
+__global__ void __launch_bounds__(kAXThreads, adj_x_min_blocks<T>()) adjoint_x_kernel(AdjArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
   T* sm = su + NV * kXCells;                // [NV][kXCells] mu
@@ -56,7 +65,7 @@ __global__ void __launch_bounds__(kXThreads) adjoint_x_kernel(AdjArgs<T> A) {
   const int64_t n = A.nx;
   const T* ub = A.u + row * A.pitch;
   const T* mb = A.mu + row * A.pitch;
-  for (int idx = threadIdx.x; idx < NV * kXCells; idx += kXThreads) {
+  for (int idx = threadIdx.x; idx < NV * kXCells; idx += kAXThreads) {
     const int v = idx / kXCells, s = idx - v * kXCells;
     if (s < ntile + 10) {
       const int64_t i = c0 - 5 + s;
@@ -66,8 +75,7 @@ __global__ void __launch_bounds__(kXThreads) adjoint_x_kernel(AdjArgs<T> A) {
     }
   }
   __syncthreads();
-  const int t = threadIdx.x;
-  if (t < ntile + 5) {
+  for (int t = threadIdx.x; t < ntile + 5; t += kAXThreads) {
     T S[6][NV], Sb[6][NV], phi[NV];
 #pragma unroll
     for (int m = 0; m < 6; ++m)
@@ -86,7 +94,7 @@ __global__ void __launch_bounds__(kXThreads) adjoint_x_kernel(AdjArgs<T> A) {
       for (int k = 0; k < NV; ++k) sc[(k * 6 + m) * kXThreads + t] = Sb[m][k];
   }
   __syncthreads();
-  if (t < ntile) {
+  for (int t = threadIdx.x; t < ntile; t += kAXThreads) {
     const int64_t c = c0 + t;
     const int64_t off = row * A.pitch + c;
 #pragma unroll

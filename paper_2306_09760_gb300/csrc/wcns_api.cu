@@ -36,10 +36,15 @@ struct wcns_ctx {
   int* d_err;
   unsigned long long* d_fallbacks;
   unsigned int* d_counters;   // [8]
+  unsigned long long* d_wave; // fused CFL maxima slots of a step's last stage (2D Euler), 2 * kWaveSlots
   double* d_out;              // [8]
   double* d_partials;         // [kMaxRedBlocks * 2]
-  // graph of one RK3 step
+  // 2D Euler: each step's last stage reduces the next step's CFL maxima (fused epilogue)
+  bool fuse_wave;
+  // graphs of one RK step: graph starts with the CFL kernel, graph_next with the step
+  // record from the maxima of the previous step
   cudaGraphExec_t graph;
+  cudaGraphExec_t graph_next;
   const void* graph_u;
   double graph_dt, graph_tend;
   // per-kernel event timing (benchmarks)
@@ -51,9 +56,9 @@ struct wcns_ctx {
 
 namespace {
 enum ProfKind { kProfSweepXRhs = 0, kProfSweepYRhs, kProfSweepXStage1D, kProfSweepXLx, kProfSweepYStage, kProfDt,
-                kProfReduce, kProfAdjX, kProfAdjY, kProfCount };
+                kProfReduce, kProfAdjX, kProfAdjY, kProfDtFused, kProfCount };
 const char* const kProfNames[kProfCount] = {"sweep_x_rhs", "sweep_y_rhs", "sweep_x_stage_1d", "sweep_x_lx_2d",
-                                            "sweep_y_stage_2d", "dt_cfl", "reduce", "adjoint_x", "adjoint_y"};
+                                            "sweep_y_stage_2d", "dt_cfl", "reduce", "adjoint_x", "adjoint_y", "dt_from_maxima"};
 }  // namespace
 
 namespace {
@@ -142,6 +147,7 @@ struct StageCoef {
   const void* X1;
   const void* X2;
   double cstage;  // the state the stage evaluates L on is at t0 + cstage * dt
+  bool last;      // the stage completes an RK step (fused CFL maxima of its output)
 };
 
 template <typename T>
@@ -189,12 +195,16 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   y.faces = &c->faces;
   y.cstage = k.cstage;
   y.tnow = c->d_t;
+  if (stage_mode && k.last && c->fuse_wave) {
+    y.wave = c->d_wave;
+    y.err = c->d_err;
+  }
   return timed(c, stage_mode ? kProfSweepYStage : kProfSweepYRhs,
                [&] { return launch_sweep_y<T>(c->gi, c->s, y, c->stream); });
 }
 
 cudaError_t rhs_into(wcns_ctx* c, const void* u, void* out) {
-  StageCoef k{0.0, 1.0, false, 0.0, 0.0, 0.0, nullptr, nullptr, 0.0};
+  StageCoef k{0.0, 1.0, false, 0.0, 0.0, 0.0, nullptr, nullptr, 0.0, false};
   return by_type(c->g.dtype, [&] { return sweeps<double>(c, u, nullptr, out, false, k); },
                  [&] { return sweeps<float>(c, u, nullptr, out, false, k); });
 }
@@ -205,8 +215,9 @@ cudaError_t stage_coef(wcns_ctx* c, const void* u, const void* un, void* out, co
 }
 
 // TVD-RK3 stage out = a*un + b*(u + dt*L(u)), u at time t0 + cstage * dt.
-cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b, double cstage) {
-  StageCoef k{a, b, false, 0.0, 0.0, 0.0, nullptr, nullptr, cstage};
+cudaError_t stage(wcns_ctx* c, const void* u, const void* un, void* out, double a, double b, double cstage,
+                  bool last = false) {
+  StageCoef k{a, b, false, 0.0, 0.0, 0.0, nullptr, nullptr, cstage, last};
   return stage_coef(c, u, un, out, k);
 }
 
@@ -229,9 +240,30 @@ cudaError_t dt_launch(wcns_ctx* c, const void* u, double dt, double t_end, bool 
   d.t = maxwave_only ? nullptr : c->d_t;
   d.steps = c->d_steps;
   d.err = c->d_err;
+  d.wave = c->fuse_wave ? c->d_wave : nullptr;
   return timed(c, kProfDt, [&] {
     return by_type(c->g.dtype, [&] { return launch_dt<double>(c->gi, d, c->stream); },
                    [&] { return launch_dt<float>(c->gi, d, c->stream); });
+  });
+}
+
+// The step record of a step whose CFL maxima the previous step's last stage reduced
+// (fused path of 2D Euler grids): the CFL kernel's step computation without reading u.
+cudaError_t dt_from_maxima(wcns_ctx* c, double dt, double t_end) {
+  DtLaunch d{};
+  d.cfl = c->p.cfl;
+  d.fixed_dt = dt;
+  d.t_end = t_end;
+  d.use_cfl = dt > 0.0 ? 0 : 1;
+  for (int k = 0; k < 2; ++k) d.adv_wave[k] = fabs(c->p.adv_speed[k]);
+  d.step = c->d_dt;
+  d.t = c->d_t;
+  d.steps = c->d_steps;
+  d.err = c->d_err;
+  d.wave = c->d_wave;
+  return timed(c, kProfDtFused, [&] {
+    return by_type(c->g.dtype, [&] { return launch_step_from_maxima<double>(c->gi, d, c->stream); },
+                   [&] { return launch_step_from_maxima<float>(c->gi, d, c->stream); });
   });
 }
 
@@ -269,26 +301,36 @@ cudaError_t adjoint_stage(wcns_ctx* c, const void* u, const void* mu, const void
 // src: where the CFL kernel reads u^n; if it is not u, the kernel also copies it into u
 // (the host-buffer path reads a mapped host buffer once).  out: where the last stage
 // writes u^(n+1) (u itself, or the mapped host buffer).
-cudaError_t rk_step_io(wcns_ctx* c, const void* src, void* u, void* out, double dt, double t_end) {
+// from_maxima (2D Euler, a step that follows a step of the same run on the same buffer):
+// the step comes from the CFL maxima the previous step's last stage reduced, instead of
+// a CFL kernel reading u^n.  On 2D Euler grids every step's last stage reduces them.
+cudaError_t rk_step_io(wcns_ctx* c, const void* src, void* u, void* out, double dt, double t_end,
+                       bool from_maxima = false) {
   cudaError_t e;
-  if ((e = dt_launch(c, src, dt, t_end, false, src != u ? u : nullptr)) != cudaSuccess) return e;
+  if (from_maxima && c->fuse_wave && src == u) {
+    if ((e = dt_from_maxima(c, dt, t_end)) != cudaSuccess) return e;
+  } else if ((e = dt_launch(c, src, dt, t_end, false, src != u ? u : nullptr)) != cudaSuccess) {
+    return e;
+  }
   if (c->p.integrator == WCNS_RK4) {
-    StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.0};
+    StageCoef k1{0.0, 1.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.0, false};
     if ((e = stage_coef(c, u, u, c->u1, k1)) != cudaSuccess) return e;
-    StageCoef k2{1.0, 0.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.5};
+    StageCoef k2{1.0, 0.0, true, 0.5, 0.0, 0.0, nullptr, nullptr, 0.5, false};
     if ((e = stage_coef(c, c->u1, u, c->u2, k2)) != cudaSuccess) return e;
-    StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr, 0.5};
+    StageCoef k3{1.0, 0.0, true, 1.0, 0.0, 0.0, nullptr, nullptr, 0.5, false};
     if ((e = stage_coef(c, c->u2, u, c->u3, k3)) != cudaSuccess) return e;
-    StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2, 1.0};
+    StageCoef k4{-1.0 / 3.0, 1.0 / 3.0, true, 1.0 / 6.0, 1.0 / 3.0, 2.0 / 3.0, c->u1, c->u2, 1.0, true};
     return stage_coef(c, c->u3, u, out, k4);
   }
   // stage times t, t + dt, t + dt/2
   if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0, 0.0)) != cudaSuccess) return e;
   if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25, 1.0)) != cudaSuccess) return e;
-  return stage(c, c->u2, u, out, 1.0 / 3.0, 2.0 / 3.0, 0.5);
+  return stage(c, c->u2, u, out, 1.0 / 3.0, 2.0 / 3.0, 0.5, true);
 }
 
-cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end) { return rk_step_io(c, u, u, u, dt, t_end); }
+cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end, bool from_maxima) {
+  return rk_step_io(c, u, u, u, dt, t_end, from_maxima);
+}
 
 // Device address of page-locked host memory registered in this context, or nullptr
 // (pageable memory, another device's allocation, or a device pointer).
@@ -304,31 +346,67 @@ void* mapped_host(const wcns_ctx* c, void* p) {
 
 void drop_graph(wcns_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_next) cudaGraphExecDestroy(c->graph_next);
   c->graph = nullptr;
+  c->graph_next = nullptr;
   c->graph_u = nullptr;
 }
 
-cudaError_t build_graph(wcns_ctx* c, void* u, double dt, double t_end) {
-  drop_graph(c);
+cudaError_t capture_step(wcns_ctx* c, void* u, double dt, double t_end, bool from_maxima, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t body = rk3_step(c, u, dt, t_end);
+  cudaError_t body = rk3_step(c, u, dt, t_end, from_maxima);
   e = cudaStreamEndCapture(c->stream, &g);
   if (body != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return body;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
+}
+
+// Graphs of one step on u: the first step of a call (CFL kernel) and, on 2D Euler grids,
+// the following ones (step from the maxima the previous step's last stage reduced).
+cudaError_t build_graph(wcns_ctx* c, void* u, double dt, double t_end) {
+  drop_graph(c);
+  cudaError_t e = capture_step(c, u, dt, t_end, false, &c->graph);
+  if (e == cudaSuccess && c->fuse_wave) e = capture_step(c, u, dt, t_end, true, &c->graph_next);
   if (e != cudaSuccess) {
-    c->graph = nullptr;
+    drop_graph(c);
     return e;
   }
   c->graph_u = u;
   c->graph_dt = dt;
   c->graph_tend = t_end;
+  return cudaSuccess;
+}
+
+// nsteps steps of u.  continuing: the previous step of this run on u was the last one
+// enqueued (its last stage reduced the CFL maxima of u), so on 2D Euler grids the first
+// step also takes its step from them.
+cudaError_t step_run(wcns_ctx* c, void* u, double dt, int32_t nsteps, double t_end, bool continuing) {
+  // Replaying a captured step graph needs a capturable stream (not the legacy default);
+  // per-kernel timing launches directly.
+  if (c->stream != nullptr && nsteps >= 2 && !c->prof_on) {
+    if (!c->graph || c->graph_u != u || c->graph_dt != dt || c->graph_tend != t_end) {
+      cudaError_t e = build_graph(c, u, dt, t_end);
+      if (e != cudaSuccess) return e;
+    }
+    for (int32_t k = 0; k < nsteps; ++k) {
+      cudaGraphExec_t g = (c->fuse_wave && (k > 0 || continuing)) ? c->graph_next : c->graph;
+      cudaError_t e = cudaGraphLaunch(g, c->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    cudaError_t e = rk3_step(c, u, dt, t_end, k > 0 || continuing);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -400,6 +478,7 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   c->gi.h[1] = g.ndim == 2 ? (g.hi[1] - g.lo[1]) / (double)g.ny : 1.0;
   c->stream = static_cast<cudaStream_t>(stream);
   c->elem = g.dtype == WCNS_F64 ? 8 : 4;
+  c->fuse_wave = g.ndim == 2 && g.nvar == 4;
   c->nelem = (size_t)g.nvar * (size_t)g.ny * (size_t)g.pitch;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess)
@@ -410,9 +489,13 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   if (e == cudaSuccess) e = cudaMalloc(&c->u2, bytes);
   if (e == cudaSuccess && g.ndim == 2) e = cudaMalloc(&c->R, bytes);
   if (e == cudaSuccess && params->integrator == WCNS_RK4) e = cudaMalloc(&c->u3, bytes);
+  if (e == cudaSuccess && c->fuse_wave)
+    e = cudaMalloc(reinterpret_cast<void**>(&c->d_wave), sizeof(unsigned long long) * 2 * kWaveSlots);
   const size_t scal_bytes = 4096 + sizeof(double) * 2 * kMaxRedBlocks;
   if (e == cudaSuccess) e = cudaMalloc(&c->scal, scal_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->scal, 0, scal_bytes, c->stream);
+  if (e == cudaSuccess && c->fuse_wave)
+    e = cudaMemsetAsync(c->d_wave, 0, sizeof(unsigned long long) * 2 * kWaveSlots, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     wcns_destroy(c);
@@ -444,16 +527,7 @@ wcns_status wcns_step(wcns_ctx* c, void* u, double dt, int32_t nsteps, double t_
   if (!c || !u || !aligned16(u) || nsteps < 0) return WCNS_ERR_ARG;
   if (dt != dt || t_end != t_end) return WCNS_ERR_ARG;
   if (nsteps == 0) return WCNS_OK;
-  // Replaying a captured step graph needs a capturable stream (not the legacy default);
-  // per-kernel timing launches directly.
-  if (c->stream != nullptr && nsteps >= 2 && !c->prof_on) {
-    if (!c->graph || c->graph_u != u || c->graph_dt != dt || c->graph_tend != t_end)
-      WCNS_TRY(build_graph(c, u, dt, t_end));
-    for (int32_t k = 0; k < nsteps; ++k) WCNS_TRY(cudaGraphLaunch(c->graph, c->stream));
-    return WCNS_OK;
-  }
-  for (int32_t k = 0; k < nsteps; ++k) WCNS_TRY(rk3_step(c, u, dt, t_end));
-  return WCNS_OK;
+  return from_cuda(step_run(c, u, dt, nsteps, t_end, false));
 }
 
 wcns_status wcns_step_host(wcns_ctx* c, void* u_host, double dt, int32_t nsteps, double t_end) {
@@ -480,8 +554,7 @@ wcns_status wcns_step_host(wcns_ctx* c, void* u_host, double dt, int32_t nsteps,
     WCNS_TRY(rk_step_io(c, hd, c->host_state, hd, dt, t_end));
   } else {
     WCNS_TRY(rk_step_io(c, hd, c->host_state, c->host_state, dt, t_end));
-    wcns_status s = wcns_step(c, c->host_state, dt, nsteps - 1, t_end);
-    if (s != WCNS_OK) return s;
+    WCNS_TRY(step_run(c, c->host_state, dt, nsteps - 1, t_end, true));
     WCNS_TRY(cudaMemcpyAsync(u_host, c->host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
   }
   WCNS_TRY(cudaStreamSynchronize(c->stream));
@@ -678,6 +751,7 @@ void wcns_destroy(wcns_ctx* c) {
   if (c->adj1) cudaFree(c->adj1);
   if (c->adj2) cudaFree(c->adj2);
   if (c->scal) cudaFree(c->scal);
+  if (c->d_wave) cudaFree(c->d_wave);
   delete c;
 }
 

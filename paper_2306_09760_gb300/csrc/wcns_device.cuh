@@ -46,6 +46,10 @@ struct StepDt {
   int zero;
 };
 
+// Slot pairs into which the last RK stage of a 2D Euler step merges the CFL maxima of the
+// state it writes (one slot per warp, modulo the count).
+constexpr int kWaveSlots = 256;
+
 // Boundary faces x-lo, x-hi, y-lo, y-hi beyond periodic / transmissive lines (Sec. 4.3):
 // 0 the direction's bc, 1 transmissive, 2 inviscid wall (mirror cell, normal momentum
 // reversed), 3 fixed state A, 4 state A for x < wall_x and a wall beyond, 5 the moving

@@ -42,6 +42,11 @@ struct SweepCall {
   const Faces<double>* faces;  // boundary faces (active == 0: the grid's bc only)
   double cstage;               // the state read is at t0 + cstage * dt of the step
   const double* tnow;          // device time (RHS evaluations)
+  // y sweep of a 2D Euler stage that completes an RK step: CFL maxima of the written
+  // state merged into the slots of wave (kWaveSlots pairs) and non-physical cells
+  // flagged in *err (else null)
+  unsigned long long* wave;
+  int* err;
 };
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
@@ -81,9 +86,13 @@ struct DtLaunch {
   double* t;
   long long* steps;
   int* err;
+  unsigned long long* wave;  // fused CFL maxima slots of a step's last stage (2 * kWaveSlots), or null
 };
 template <typename T>
 cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st);
+// The step record from the maxima in d.wave (reduced by the previous step's last stage).
+template <typename T>
+cudaError_t launch_step_from_maxima(const GridInfo& g, const DtLaunch& d, cudaStream_t st);
 
 // App. A weight statistics of one evaluation of L(u), accumulated into
 // hist[2][3][nbins] (device, 64-bit counters).

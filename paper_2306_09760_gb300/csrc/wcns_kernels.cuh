@@ -39,6 +39,13 @@ struct SweepArgs {
   T inv_h;
   SchemeT<T> s;
   unsigned long long* fallbacks;   // interfaces that fell back to first order
+  // y sweep of a 2D stage that completes an RK step (or null): the CFL maxima of the
+  // cells it writes, max |u| + c and max |v| + c, merged per warp with atomicMax into
+  // kWaveSlots slot pairs (bit patterns of non-negative doubles, whose integer order is
+  // their numeric order; spreading the warps over slots keeps the atomics uncontended);
+  // a non-physical written cell sets bit 0 of *err
+  unsigned long long* wave;
+  int* err;
   Faces<T> f;                      // boundary faces beyond periodic / transmissive lines
   double cstage;                   // stage time t0 + cstage * dt of the state read (faces)
   const double* tnow;              // device time (faces, RHS without a step)
@@ -65,6 +72,42 @@ __device__ __forceinline__ T reload(const T* p) { return *static_cast<const vola
 __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
   unsigned m = __ballot_sync(0xffffffffu, fb);
   if (m && (threadIdx.x & 31) == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+// Signal speeds |u| + c and |v| + c of one cell (rho, rho u, rho v, E) in the state's own
+// precision; false for a non-physical state (rho <= 0, p <= 0 or NaN).  The CFL kernel
+// and the fused stage epilogue share it, so both reduce the same values.
+template <typename T>
+__device__ __forceinline__ bool cell_wave(T rho, T mu, T mv, T E, T g, T gm1, T& wx, T& wy) {
+  const T inv = T(1) / rho;
+  const T ux = mu * inv, vy = mv * inv;
+  const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
+  if (!(rho > T(0)) || !(p > T(0))) return false;
+  const T cs = Num<T>::sqrt_(g * p * inv);
+  wx = Num<T>::abs_(ux) + cs;
+  wy = Num<T>::abs_(vy) + cs;
+  return true;
+}
+
+// Warp maxima of two non-negative values (every lane of the warp calls it; lanes with
+// nothing to add pass 0) merged into one of kWaveSlots slot pairs of wave with
+// atomicMax, and the warp's non-physical flag into *err.
+template <typename T>
+__device__ __forceinline__ void warp_wave(T mx, T my, bool bad, unsigned long long* wave, int* err) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  const bool anybad = __any_sync(0xffffffffu, bad);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) {
+    const unsigned slot = (((unsigned)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y / 32) +
+                           (unsigned)(tid >> 5)) % kWaveSlots;
+    atomicMax(&wave[2 * slot], (unsigned long long)__double_as_longlong((double)mx));
+    atomicMax(&wave[2 * slot + 1], (unsigned long long)__double_as_longlong((double)my));
+    if (anybad) atomicOr(err, 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -316,21 +359,38 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
 #pragma unroll
     for (int k = 0; k < NV; ++k) rv[q][k] = on ? A.R[k * A.fstride + off] : T(0);
   }
+  T wmx = T(0), wmy = T(0);
+  bool wbad = false;
 #pragma unroll
   for (int q = 0; q < kYPer; ++q) {
     const int t = threadIdx.y + kYRowsT * q;
     if (tx < ncol && t < ntile) {
       const int64_t off = (r0 + t) * A.pitch + c0 + tx;
+      T val[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const T* f = sf + (k * kYIfc + t) * kYCols + tx;
         T Ly = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
                                   f[5 * kYCols], A.inv_h);
         // RHS: R = L_x.  Stage: R = a*un + b*(u + dt*L_x) from the x sweep.
-        A.out[k * A.fstride + off] =
-            (MODE == kWriteL) ? rv[q][k] + Ly : rv[q][k] + ((A.general ? A.e : A.b) * dt) * Ly;
+        val[k] = (MODE == kWriteL) ? rv[q][k] + Ly : rv[q][k] + ((A.general ? A.e : A.b) * dt) * Ly;
+        A.out[k * A.fstride + off] = val[k];
+      }
+      if constexpr (MODE == kStage && NV == 4) {
+        if (A.wave) {
+          T wx, wy;
+          if (cell_wave<T>(val[0], val[1], val[2], val[3], A.s.gamma, A.s.gm1, wx, wy)) {
+            wmx = fmax(wmx, wx);
+            wmy = fmax(wmy, wy);
+          } else {
+            wbad = true;
+          }
+        }
       }
     }
+  }
+  if constexpr (MODE == kStage && NV == 4) {
+    if (A.wave) warp_wave<T>(wmx, wmy, wbad, A.wave, A.err);  // the same for every thread of the launch
   }
 }
 
@@ -392,7 +452,64 @@ struct DtArgs {
   double* t;
   long long* steps;
   int* err;              // bit 0: non-physical state
+  // fused CFL maxima of a step's last stage (kWaveSlots slot pairs): cleared by the CFL
+  // kernel, read and cleared by step_from_maxima_kernel (or null)
+  unsigned long long* wave;
 };
+
+// The step of an RK step from the signal-speed maxima gx, gy (the CFL kernel's last block,
+// or the maxima the previous step's last stage reduced): dt = cfl / sum_d(max_d / h_d)
+// (or the fixed step), zero once a non-physical state was seen, clipped at t_end; writes
+// the step record and advances the device time.  One thread.
+__device__ __forceinline__ void finish_step(const DtArgs& A, double gx, double gy) {
+  double d;
+  if (!A.use_cfl) {
+    d = A.fixed_dt;
+  } else {
+    if (A.nvar == 1) { gx = A.adv_wave[0]; gy = A.adv_wave[1]; }
+    double s = gx / A.hx;
+    if (A.ndim == 2) s += gy / A.hy;
+    d = A.cfl / s;
+  }
+  if (__ldcg(A.err) & 1) d = 0.0;  // a non-physical state freezes the run (reported at sync)
+  double t = *A.t;
+  if (A.t_end > 0.0) {
+    double rem = A.t_end - t;
+    if (d > rem) d = rem;
+    if (!(d > 0.0)) d = 0.0;
+  }
+  A.step->dt = d;
+  A.step->t0 = t;
+  A.step->dt32 = (float)d;
+  A.step->zero = (d == 0.0);
+  if (d > 0.0) {
+    *A.t = (A.t_end > 0.0 && d == A.t_end - t) ? A.t_end : t + d;
+    *A.steps += 1;
+  }
+}
+
+// Step record of an RK step whose CFL maxima the previous step's last stage merged into
+// the slots (the fused epilogue of the y sweep): one block takes their maxima, clears the
+// slots for this step's last stage and computes the step.
+template <typename T>
+__global__ void __launch_bounds__(kWaveSlots) step_from_maxima_kernel(DtArgs A) {
+  __shared__ double sx[kWaveSlots / 32], sy[kWaveSlots / 32];
+  const int i = threadIdx.x;
+  double gx = __longlong_as_double((long long)A.wave[2 * i]);
+  double gy = __longlong_as_double((long long)A.wave[2 * i + 1]);
+  A.wave[2 * i] = 0ull;
+  A.wave[2 * i + 1] = 0ull;
+  gx = warp_max(gx);
+  gy = warp_max(gy);
+  if ((i & 31) == 0) {
+    sx[i >> 5] = gx;
+    sy[i >> 5] = gy;
+  }
+  __syncthreads();
+  if (i != 0) return;
+  for (int w = 0; w < kWaveSlots / 32; ++w) { gx = fmax(gx, sx[w]); gy = fmax(gy, sy[w]); }
+  finish_step(A, gx, gy);
+}
 
 template <typename T, int NV>
 __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
@@ -448,13 +565,10 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
             if (q * VW + l >= A.nx) break;
             // wave speeds in the state's own precision
             const T rho = v[j][0][l], mu = v[j][1][l], mv = (NV == 4) ? v[j][2][l] : T(0), E = v[j][NV - 1][l];
-            const T inv = T(1) / rho;
-            const T ux = mu * inv, vy = mv * inv;
-            const T p = gm1 * (E - T(0.5) * rho * (ux * ux + vy * vy));
-            if (!(rho > T(0)) || !(p > T(0))) { bad = 1; continue; }
-            const T cs = Num<T>::sqrt_(g * p * inv);
-            mxT = fmax(mxT, Num<T>::abs_(ux) + cs);
-            myT = fmax(myT, Num<T>::abs_(vy) + cs);
+            T wx, wy;
+            if (!cell_wave<T>(rho, mu, mv, E, g, gm1, wx, wy)) { bad = 1; continue; }
+            mxT = fmax(mxT, wx);
+            myT = fmax(myT, wy);
           }
         }
       }
@@ -508,30 +622,9 @@ __global__ void __launch_bounds__(kRedThreads) dt_kernel(DtArgs A) {
     A.dt_out[1] = gy;
     return;
   }
-  double d;
-  if (!A.use_cfl) {
-    d = A.fixed_dt;
-  } else {
-    if (NV == 1) { gx = A.adv_wave[0]; gy = A.adv_wave[1]; }
-    double s = gx / A.hx;
-    if (A.ndim == 2) s += gy / A.hy;
-    d = A.cfl / s;
-  }
-  if (__ldcg(A.err) & 1) d = 0.0;  // a non-physical state freezes the run (reported at sync)
-  double t = *A.t;
-  if (A.t_end > 0.0) {
-    double rem = A.t_end - t;
-    if (d > rem) d = rem;
-    if (!(d > 0.0)) d = 0.0;
-  }
-  A.step->dt = d;
-  A.step->t0 = t;
-  A.step->dt32 = (float)d;
-  A.step->zero = (d == 0.0);
-  if (d > 0.0) {
-    *A.t = (A.t_end > 0.0 && d == A.t_end - t) ? A.t_end : t + d;
-    *A.steps += 1;
-  }
+  if (A.wave)  // this step's last stage merges the next step's maxima from zero
+    for (int k = 0; k < 2 * kWaveSlots; ++k) A.wave[k] = 0ull;
+  finish_step(A, gx, gy);
 }
 
 // ---------------------------------------------------------------------------

@@ -97,6 +97,8 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   if (c.faces) A.f = faces_as<T>(*c.faces);
   A.cstage = c.cstage;
   A.tnow = c.tnow;
+  A.wave = c.wave;
+  A.err = c.err;
   return A;
 }
 
@@ -250,12 +252,12 @@ cudaError_t launch_adjoint_x(const GridInfo& g, const Scheme& s, const AdjCall<T
   dim3 grid((unsigned)((g.nx + kXTile - 1) / kXTile), (unsigned)g.ny);
   switch (g.nvar) {
     case 3:
-      if (c.combine) adjoint_x_kernel<T, 3, kAdjCombine><<<grid, kXThreads, adj_x_smem<T, 3>(), st>>>(A);
-      else adjoint_x_kernel<T, 3, kAdjWrite><<<grid, kXThreads, adj_x_smem<T, 3>(), st>>>(A);
+      if (c.combine) adjoint_x_kernel<T, 3, kAdjCombine><<<grid, kAXThreads, adj_x_smem<T, 3>(), st>>>(A);
+      else adjoint_x_kernel<T, 3, kAdjWrite><<<grid, kAXThreads, adj_x_smem<T, 3>(), st>>>(A);
       break;
     case 4:
-      if (c.combine) adjoint_x_kernel<T, 4, kAdjCombine><<<grid, kXThreads, adj_x_smem<T, 4>(), st>>>(A);
-      else adjoint_x_kernel<T, 4, kAdjWrite><<<grid, kXThreads, adj_x_smem<T, 4>(), st>>>(A);
+      if (c.combine) adjoint_x_kernel<T, 4, kAdjCombine><<<grid, kAXThreads, adj_x_smem<T, 4>(), st>>>(A);
+      else adjoint_x_kernel<T, 4, kAdjWrite><<<grid, kAXThreads, adj_x_smem<T, 4>(), st>>>(A);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -307,7 +309,7 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
   A.fixed_dt = d.fixed_dt; A.t_end = d.t_end;
   A.adv_wave[0] = d.adv_wave[0]; A.adv_wave[1] = d.adv_wave[1];
   A.partials = d.partials; A.counter = d.counter; A.dt_out = d.dt_out; A.step = d.step; A.t = d.t;
-  A.steps = d.steps; A.err = d.err;
+  A.steps = d.steps; A.err = d.err; A.wave = d.wave;
   int blocks = 1;
   A.bpr = 1;
   if (g.nvar > 1) {
@@ -333,6 +335,18 @@ cudaError_t launch_dt(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
     case 4: dt_kernel<T, 4><<<blocks, kRedThreads, 0, st>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step_from_maxima(const GridInfo& g, const DtLaunch& d, cudaStream_t st) {
+  DtArgs A{};
+  A.nvar = g.nvar; A.ndim = g.ndim; A.use_cfl = d.use_cfl;
+  A.cfl = d.cfl; A.hx = g.h[0]; A.hy = g.h[1]; A.fixed_dt = d.fixed_dt; A.t_end = d.t_end;
+  A.adv_wave[0] = d.adv_wave[0]; A.adv_wave[1] = d.adv_wave[1];
+  A.step = d.step; A.t = d.t; A.steps = d.steps; A.err = d.err; A.wave = d.wave;
+  if (!A.wave || !A.t) return cudaErrorInvalidValue;
+  step_from_maxima_kernel<T><<<1, kWaveSlots, 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -437,6 +451,7 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
   template cudaError_t launch_sweep_x<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
                                          cudaStream_t);                                              \
   template cudaError_t launch_dt<T>(const GridInfo&, const DtLaunch&, cudaStream_t);                 \
+  template cudaError_t launch_step_from_maxima<T>(const GridInfo&, const DtLaunch&, cudaStream_t);   \
   template cudaError_t launch_weight_hist<T>(const GridInfo&, const Scheme&, const Faces<double>&,  \
                                              const double*, const void*, int, unsigned long long*,   \
                                              cudaStream_t);                                          \
