@@ -78,6 +78,10 @@ struct SchemeT {
   // d_k, so Eq. 20 returns the ideal weights exactly; they sum to exactly 1, so the
   // renormalised weights are the ideal weights, which the kernels then use directly.
   T ideal_margin[3];
+  // The same test on the Z ratios before normalisation (0 = off): where every ratio
+  // r_k^p of Eq. 14 is below ideal_ratio, each Z weight lies within d_k * ideal_ratio
+  // < ideal_margin[k] of d_k (the weights are d_k (1 + r_k^p) / (1 + sum_l d_l r_l^p)).
+  T ideal_ratio;
   T speed[2];
   T null0[3], null1[4], null2[3];
   T ideal[3], ctrl0[2], ctrl1[3], ctrl2[2];
@@ -131,6 +135,7 @@ inline Faces<T> faces_as(const Faces<double>& f) {
 template <typename T>
 inline void ideal_margins(const Scheme& s, SchemeT<T>& r) {
   for (int k = 0; k < 3; ++k) r.ideal_margin[k] = T(0);
+  r.ideal_ratio = T(0);
   if (s.weights != 2 || r.xi_small) return;
   if (T(T(s.ideal[0]) + T(s.ideal[1])) + T(s.ideal[2]) != T(1)) return;
   const double sat = (sizeof(T) == 4 ? 9.1 : 20.0 + 1.0e-4 + 4.0e-7 * s.xi) / s.xi;
@@ -152,7 +157,12 @@ inline void ideal_margins(const Scheme& s, SchemeT<T>& r) {
     m[k] = (d - lo < hi - d ? d - lo : hi - d) * (1.0 - 1.0e-6) - sat * (1.0 + 1.0e-3) - 1.0e-6;
     if (!(m[k] > 0.0)) return;
   }
-  for (int k = 0; k < 3; ++k) r.ideal_margin[k] = T(m[k]);
+  double ratio = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    r.ideal_margin[k] = T(m[k]);
+    ratio = m[k] / s.ideal[k] < ratio ? m[k] / s.ideal[k] : ratio;
+  }
+  r.ideal_ratio = T(ratio * (1.0 - 1.0e-3));
 }
 
 template <typename T>
@@ -545,13 +555,18 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
       r0 = Num<T>::z_ratio(tau, b0); r1 = Num<T>::z_ratio(tau, b1); r2 = Num<T>::z_ratio(tau, b2);
     }
     if (zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
-    T a0 = d0 * (T(1) + r0), a1 = d1 * (T(1) + r1), a2 = d2 * (T(1) + r2);
-    const T isa = Num<T>::rcp_(a0 + a1 + a2);
-    w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
-    if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
-    if (weights == 2 && s.ideal_margin[0] > T(0) && Num<T>::abs_(w0 - d0) < s.ideal_margin[0] &&
-        Num<T>::abs_(w1 - d1) < s.ideal_margin[1] && Num<T>::abs_(w2 - d2) < s.ideal_margin[2]) {
-      // inside the ideal plateaus: Eq. 20 and the renormalisation give the ideal weights
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    const bool small = weights == 2 && !wz && r0 < s.ideal_ratio && r1 < s.ideal_ratio && r2 < s.ideal_ratio;
+    if (!small) {
+      a0 = d0 * (T(1) + r0); a1 = d1 * (T(1) + r1); a2 = d2 * (T(1) + r2);
+      const T isa = Num<T>::rcp_(a0 + a1 + a2);
+      w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
+      if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
+    }
+    if (small || (weights == 2 && s.ideal_margin[0] > T(0) && Num<T>::abs_(w0 - d0) < s.ideal_margin[0] &&
+                  Num<T>::abs_(w1 - d1) < s.ideal_margin[1] && Num<T>::abs_(w2 - d2) < s.ideal_margin[2])) {
+      // inside the ideal plateaus (tested on the ratios, or on the weights): Eq. 20 and the
+      // renormalisation give the ideal weights
       w0 = d0; w1 = d1; w2 = d2;
     } else if (weights >= 2) {
       bool keep = false;

@@ -126,6 +126,15 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
     split(r1, t0, t1); r1 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     split(r2, t0, t1); r2 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     if (zp == 2) { r0 = mul(r0, r0); r1 = mul(r1, r1); r2 = mul(r2, r2); }
+    if (weights == 2) {
+      // every ratio of both lanes below ideal_ratio: the Z weights lie inside the ideal
+      // plateaus of Eq. 20 (see SchemeT::ideal_ratio), so the mapped and renormalised
+      // weights are the ideal ones, without normalising the Z weights first
+      float a, b, c, d, e, f;
+      split(r0, a, b); split(r1, c, d); split(r2, e, f);
+      const float q = s.ideal_ratio;
+      if (a < q && b < q && c < q && d < q && e < q && f < q) return fma(bc(d2), q2, fma(bc(d1), q1, mul(bc(d0), q0)));
+    }
     const P2 a0 = fma(bc(d0), r0, bc(d0)), a1 = fma(bc(d1), r1, bc(d1)), a2 = fma(bc(d2), r2, bc(d2));
     const P2 isa = rcp(add(add(a0, a1), a2));
     w0 = mul(a0, isa); w1 = mul(a1, isa); w2 = mul(a2, isa);
