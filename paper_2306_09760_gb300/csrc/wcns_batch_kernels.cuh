@@ -72,16 +72,7 @@ __global__ void __launch_bounds__(NT) batch_stage_kernel(BatchStageArgs<T> A) {
           for (int k = 0; k < NV; ++k) S[m][k] = su[k][t + m];
         T F[NV];
         if constexpr (sizeof(T) == 4 && NV > 1) {
-          bool exact;
-          fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
-          if (exact) {
-            T E[6][NV];
-#pragma unroll
-            for (int m = 0; m < 6; ++m)
-#pragma unroll
-              for (int k = 0; k < NV; ++k) E[m][k] = reload(&su[k][t + m]);
-            fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
-          }
+          fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
         } else {
           fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
         }

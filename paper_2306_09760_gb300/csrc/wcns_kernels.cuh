@@ -64,11 +64,6 @@ __device__ __forceinline__ double sweep_time(const SweepArgs<T>& A) {
 // then adds b*dt*L_y, so its epilogue reads one array instead of two.
 enum SweepMode { kWriteL = 0, kStage = 1 };
 
-// A second read of a staged value, issued as a fresh shared-memory load so that the
-// first copy need not stay live in registers until the rare path that wants it again.
-template <typename T>
-__device__ __forceinline__ T reload(const T* p) { return *static_cast<const volatile T*>(p); }
-
 __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
   unsigned m = __ballot_sync(0xffffffffu, fb);
   if (m && (threadIdx.x & 31) == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
@@ -200,16 +195,7 @@ __global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(Swee
         for (int k = 0; k < NV; ++k) S[m][k] = su[k * CELLS + t + m];
       T F[NV];
       if constexpr (sizeof(T) == 4 && NV > 1) {
-        bool exact;
-        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F, exact);
-        if (exact) {
-          T E[6][NV];
-#pragma unroll
-          for (int m = 0; m < 6; ++m)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) E[m][k] = reload(su + k * CELLS + t + m);
-          fb = interface_flux<T, NV, FIX>(E, A.s, 0, F);
-        }
+        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 0, F);
       } else {
         fb = interface_flux<T, NV, FIX>(S, A.s, 0, F);
       }
@@ -321,20 +307,7 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
       }
       T F[NV];
       if constexpr (sizeof(T) == 4 && NV > 1) {
-        bool exact;
-        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 1, F, exact);
-        if (exact) {
-          T E[6][NV];
-#pragma unroll
-          for (int m = 0; m < 6; ++m) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-              const int src = (NV == 4 && k == 1) ? p1 : ((NV == 4 && k == 2) ? p2 : k);
-              E[m][k] = reload(su + (src * kYCells + t + m) * kYCols + tx);
-            }
-          }
-          fb = interface_flux<T, NV, FIX>(E, A.s, 1, F);
-        }
+        fb = pk::interface_flux_pair<NV, FIX>(S, A.s, 1, F);
       } else {
         fb = interface_flux<T, NV, FIX>(S, A.s, 1, F);
       }

@@ -77,10 +77,8 @@ __device__ __forceinline__ P2 rcp(P2 a) {
 
 // Eq. 5-15 and the option-dependent weight maps for the pair (left, right) of
 // mirrored stencils v0..v4; returns the two interpolated midpoint values (Eq. 6).
-// dmin: lowered to the smallest |w - null| of the FE map's saturated evaluations (Eq. 20);
-// the caller redoes the interface on the exact path when it falls below sat_dist.
 template <int FIX>
-__device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const SchemeT<float>& s, float& dmin) {
+__device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const SchemeT<float>& s) {
   const int weights = WCNS_OPT(FIX, s, weights);
   const int zp = WCNS_OPT(FIX, s, zp);
   const int renorm = WCNS_OPT(FIX, s, renorm);
@@ -126,7 +124,7 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
     split(r1, t0, t1); r1 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     split(r2, t0, t1); r2 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     if (zp == 2) { r0 = mul(r0, r0); r1 = mul(r1, r1); r2 = mul(r2, r2); }
-    if (weights == 2) {
+    if (weights == 2 && (Fixed<FIX>::on || s.ideal_ratio > 0.0f)) {
       // every ratio of both lanes below ideal_ratio: the Z weights lie inside the ideal
       // plateaus of Eq. 20 (see SchemeT::ideal_ratio), so the mapped and renormalised
       // weights are the ideal ones, without normalising the Z weights first
@@ -164,19 +162,29 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
         keep_r = (r0s >= d0 - cv) && (r0s <= d0 + cv) && (r1s >= d1 - cv) && (r1s <= d1 + cv) &&
                  (r2s >= d2 - cv) && (r2s <= d2 + cv);
       }
-      // Eq. 20 on each weight of each lane: the saturated staircase, with the distance
-      // to the null points kept for one test per interface (the exponential form of the
-      // map at small xi is evaluated here directly)
+      // Eq. 20 on each weight of each lane: the saturated staircase where every tanh
+      // term of the lane's three maps is saturated (no weight within sat_dist of a null
+      // point), else the exact map for that lane (the exponential form of the map at small
+      // xi is evaluated here directly)
       constexpr int FAM = Fixed<FIX>::on ? 0 : -1;
       if (!Fixed<FIX>::on && s.xi_small) {
         if (!keep_l) fe_map_all<float, FAM>(l0, l1, l2, s);
         if (!keep_r) fe_map_all<float, FAM>(r0s, r1s, r2s, s);
       } else {
-        const float dl = keep_l ? 3.0e38f : fe_null_distance<float, FAM>(l0, l1, l2, s);
-        const float dr = keep_r ? 3.0e38f : fe_null_distance<float, FAM>(r0s, r1s, r2s, s);
-        dmin = fminf(dmin, fminf(dl, dr));
-        if (!keep_l) fe_staircase<float, FAM>(l0, l1, l2, s);
-        if (!keep_r) fe_staircase<float, FAM>(r0s, r1s, r2s, s);
+        if (!keep_l) {
+          if (fe_null_distance<float, FAM>(l0, l1, l2, s) >= s.sat_dist) {
+            fe_staircase<float, FAM>(l0, l1, l2, s);
+          } else {
+            l0 = fe_map_slow<float>(0, l0, s); l1 = fe_map_slow<float>(1, l1, s); l2 = fe_map_slow<float>(2, l2, s);
+          }
+        }
+        if (!keep_r) {
+          if (fe_null_distance<float, FAM>(r0s, r1s, r2s, s) >= s.sat_dist) {
+            fe_staircase<float, FAM>(r0s, r1s, r2s, s);
+          } else {
+            r0s = fe_map_slow<float>(0, r0s, s); r1s = fe_map_slow<float>(1, r1s, s); r2s = fe_map_slow<float>(2, r2s, s);
+          }
+        }
       }
       const P2 m0 = mk(l0, r0s), m1 = mk(l1, r1s), m2 = mk(l2, r2s);
       // Eq. 6 on the mapped weights, renormalised (kept lanes are already normalised)
@@ -265,17 +273,13 @@ __device__ __forceinline__ RoeAvg<float, NV> roe_pair(const PrimPair<NV>& q, flo
 
 // Midpoint flux at one interface (single precision, Euler systems), the packed
 // counterpart of interface_flux.  Returns true if the interpolated states were
-// non-physical and the interface fell back to (U_i, U_{i+1}).  Sets `exact` (and leaves
-// F unset) when the interface needs the exact FE map: the caller then calls
-// interface_flux on the same stencil.
+// non-physical and the interface fell back to (U_i, U_{i+1}).
 template <int NV, int FIX>
 __device__ __forceinline__ bool interface_flux_pair(const float (&S)[6][NV], const SchemeT<float>& s, int dir,
-                                                   float (&F)[NV], bool& exact) {
+                                                   float (&F)[NV]) {
   static_assert(NV == 3 || NV == 4, "packed path is for the Euler systems");
-  exact = false;
   if (WCNS_OPT(FIX, s, family) == 1) return interface_flux<float, NV, FIX>(S, s, dir, F);  // App. B, scalar
   const float gm1 = s.gm1;
-  float dmin = 3.0e38f;
   P2 U[NV];  // (left, right) interpolated states
   if (WCNS_OPT(FIX, s, characteristic)) {
     P2 Uc[NV];
@@ -295,20 +299,13 @@ __device__ __forceinline__ bool interface_flux_pair(const float (&S)[6][NV], con
     P2 WI[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      WI[k] = weno_pair<FIX>(W[0][k], W[1][k], W[2][k], swap(W[2][k]), swap(W[1][k]), s, dmin);
+      WI[k] = weno_pair<FIX>(W[0][k], W[1][k], W[2][k], swap(W[2][k]), swap(W[1][k]), s);
     unproject_pair<NV>(cb, WI, U);
   } else {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
       U[k] = weno_pair<FIX>(mk(S[0][k], S[5][k]), mk(S[1][k], S[4][k]), mk(S[2][k], S[3][k]),
-                            mk(S[3][k], S[2][k]), mk(S[4][k], S[1][k]), s, dmin);
-  }
-  // Some FE tanh term of this interface is not saturated (a weight within sat_dist of a
-  // null point; rare at large xi): the caller runs the interface on the exact scalar
-  // path from its staged stencil (not kept live here).
-  if (!(dmin >= s.sat_dist)) {
-    exact = true;
-    return false;
+                            mk(S[3][k], S[2][k]), mk(S[4][k], S[1][k]), s);
   }
   // admissibility of the interpolated states (positive density and pressure)
   const PrimPair<NV> q = prim_pair<NV>(U, gm1);
