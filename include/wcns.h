@@ -255,6 +255,15 @@ wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void
 wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const void* lam_np1,
                               void* lam_n);
 
+/* The device reciprocal behind every double-precision division of the sweeps and the CFL
+ * step computation: out[i] = 1 / x[i] by two steps of Newton's iteration for the
+ * reciprocal from the reciprocal unit's approximation.  No counterpart in the paper: it
+ * lets a caller check that arithmetic against IEEE division (it differs by at most a
+ * couple of ulps).  x, out: device arrays of n doubles, 8-byte aligned, owned by the
+ * caller; inputs normal, finite and nonzero.  Asynchronous on `stream` (NULL: default
+ * stream).  WCNS_ERR_ARG for a NULL pointer with n > 0, misalignment or n < 0. */
+wcns_status wcns_reciprocal_f64(const double* x, double* out, int64_t n, void* stream);
+
 /* Synchronises the context stream and returns (then clears) the sticky device
  * error; *nonphysical_interfaces (may be NULL) receives the number of interfaces
  * whose interpolated states fell back to the cell states since the last call. */

@@ -46,12 +46,13 @@ constexpr size_t adj_x_smem() { return sizeof(T) * NV * (2 * kXCells + 6 * kXThr
 
 // The x adjoint covers the forward tile (kXThreads interfaces, kXTile cells) with
 // kAXThreads threads, two interfaces each: on the 512^2 adjoint workload 128-thread
-// blocks (four resident per SM in single precision) ran 0.171 ms per launch against 0.214
-// for 256 threads with one interface each (the block waits on its slowest warp's reverse
-// sweep at the barrier) and 0.275 for 64 threads with four each.
+// blocks ran 0.171 ms per launch against 0.214 for 256 threads with one interface each
+// (the block waits on its slowest warp's reverse sweep at the barrier) and 0.275 for 64
+// threads with four each.  Single precision asks for six resident blocks (at most 80
+// registers; a few spills): 0.150 ms against 0.173 at four.
 constexpr int kAXThreads = 128;
 template <typename T>
-constexpr int adj_x_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
+constexpr int adj_x_min_blocks() { return sizeof(T) == 4 ? 6 : 1; }
 
 template <typename T, int NV, int MODE>
 __global__ void __launch_bounds__(kAXThreads, adj_x_min_blocks<T>()) adjoint_x_kernel(AdjArgs<T> A) {

@@ -412,6 +412,13 @@ cudaError_t step_run(wcns_ctx* c, void* u, double dt, int32_t nsteps, double t_e
 
 }  // namespace
 
+namespace {
+__global__ void reciprocal_f64_kernel(const double* x, double* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = Num<double>::rcp_(x[i]);
+}
+}  // namespace
+
 extern "C" {
 
 const char* wcns_status_string(wcns_status s) {
@@ -691,6 +698,15 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
   WCNS_TRY(reverse_stage(c->u1, c->adj1, nullptr, 0.0, nullptr, 0.0, 0.25, c->adj2));
   WCNS_TRY(reverse_stage(u_n, c->adj2, lam_np1, 1.0 / 3.0, c->adj1, 0.75, 1.0, lam_n));
   return WCNS_OK;
+}
+
+wcns_status wcns_reciprocal_f64(const double* x, double* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return WCNS_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(x) & 7u) || (reinterpret_cast<uintptr_t>(out) & 7u)) return WCNS_ERR_ARG;
+  if (n == 0) return WCNS_OK;
+  const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  reciprocal_f64_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n);
+  return from_cuda(cudaGetLastError());
 }
 
 wcns_status wcns_sync_status(wcns_ctx* c, int64_t* nonphysical) {

@@ -205,6 +205,23 @@ template <> struct Fixed<1> {
 // Small math helpers
 // ---------------------------------------------------------------------------
 template <typename T> struct Num;
+// 1/y in double precision by Newton's iteration for the reciprocal, x <- x + x (1 - y x)
+// (each step squares the relative error), from the reciprocal unit's approximation
+// (PTX rcp.approx.ftz.f64) with two steps, each two fused multiply-adds.  On GB300 a
+// double-precision division is a longer sequence on the FP64 pipe, which is the roof of
+// the FP64 sweeps; x * rcp_nr(y) differs from x / y by at most a couple of ulps
+// (checked against IEEE division through wcns_reciprocal_f64).  Normal, finite y only
+// (the scheme divides by densities, sums of positive weights and nonzero wave-speed
+// differences).
+__device__ __forceinline__ double rcp_nr(double y) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(y));
+  double e = fma(-y, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-y, x, 1.0);
+  return fma(x, e, x);
+}
+
 template <> struct Num<double> {
   // |z| at and beyond which tanh(z) rounds to +-1 exactly in double precision
   // (1 - tanh(20) = 8.5e-18 < half an ulp of 1).
@@ -212,9 +229,14 @@ template <> struct Num<double> {
   WCNS_HD static double tanh_(double z) { return tanh(z); }
   WCNS_HD static double sqrt_(double x) { return sqrt(x); }
   WCNS_HD static double abs_(double x) { return fabs(x); }
+#ifdef __CUDA_ARCH__
+  WCNS_HD static double div_(double x, double y) { return x * rcp_nr(y); }
+  WCNS_HD static double rcp_(double x) { return rcp_nr(x); }
+#else
   WCNS_HD static double div_(double x, double y) { return x / y; }
   WCNS_HD static double rcp_(double x) { return 1.0 / x; }
-  WCNS_HD static double z_ratio(double tau, double b) { return tau / b; }
+#endif
+  WCNS_HD static double z_ratio(double tau, double b) { return div_(tau, b); }
 };
 template <> struct Num<float> {
   // 1 - tanh(9.1) = 2.5e-8 < half an ulp of 1 in single precision.
@@ -549,7 +571,7 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
     const T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
     if constexpr (sizeof(T) == 8) {
       // one division for the three ratios (the product of three IS + eps stays in range)
-      const T q = tau / (b0 * b1 * b2);
+      const T q = Num<T>::div_(tau, b0 * b1 * b2);
       r0 = q * (b1 * b2); r1 = q * (b0 * b2); r2 = q * (b0 * b1);
     } else {
       r0 = Num<T>::z_ratio(tau, b0); r1 = Num<T>::z_ratio(tau, b1); r2 = Num<T>::z_ratio(tau, b2);

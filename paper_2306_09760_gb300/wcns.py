@@ -89,6 +89,7 @@ def load():
         "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
         "wcns_set_faces": (st, [vp, vp]),
         "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
+        "wcns_reciprocal_f64": (st, [vp, vp, ctypes.c_int64, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
         "wcns_status_string": (ctypes.c_char_p, [st]),
         "wcns_profile_enable": (st, [vp, ctypes.c_int32]),
@@ -191,6 +192,12 @@ def wcns_reduce_noalloc(grid: wcns_grid, a, b, what: int, out_dev, stream=None):
     """Context-free, allocation-free reduction; `out_dev` is a device buffer of nvar doubles."""
     _check(load().wcns_reduce_noalloc(ctypes.byref(grid), _ptr(a), _ptr(b), int(what), _stream_handle(stream),
                                       _ptr(out_dev)), "wcns_reduce_noalloc")
+
+
+def wcns_reciprocal_f64(x, out, stream=None):
+    """The library's double-precision device reciprocal applied to a device tensor."""
+    _check(load().wcns_reciprocal_f64(_ptr(x), _ptr(out), int(x.numel()), _stream_handle(stream)),
+           "wcns_reciprocal_f64")
 
 
 def wcns_weight_hist(ctx, u, nbins: int, hist):

@@ -177,7 +177,9 @@ def test_1d_4096_steps(W, stream, make):
     u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=150)
     ur, tr, takenr, _ = oracle.step(P, nsteps=150)
     assert taken == takenr == 150 and abs(t - tr) <= 1e-14 * tr
-    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=150)[0], P.u0, P.name)
+    from parity import noisy_steps
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=150)[0], P.u0, P.name,
+            run_noisy=lambda: noisy_steps(P, 150))
     u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=150)
     assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
 
@@ -186,7 +188,9 @@ def test_2d_steps(W, stream):
     P = inputs.riemann2d(300, seed=0, ny=130)
     u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=20)
     ur, tr, takenr, _ = oracle.step(P, nsteps=20)
-    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=20)[0], P.u0, "riemann2d 20 steps")
+    from parity import noisy_steps
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=20)[0], P.u0, "riemann2d 20 steps",
+            run_noisy=lambda: noisy_steps(P, 20))
     u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=20)
     assert np.all(l1(u32, ur) < 1e-3), l1(u32, ur)
 
@@ -199,7 +203,9 @@ def test_riemann2d_256_100_steps(W, stream):
     u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=100)
     ur, tr, takenr, _ = oracle.step(P, nsteps=100)
     assert taken == takenr == 100
-    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=100)[0], P.u0, "riemann2d 256^2 100 steps")
+    from parity import noisy_steps
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=100)[0], P.u0, "riemann2d 256^2 100 steps",
+            run_noisy=lambda: noisy_steps(P, 100))
     u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=100)
     assert np.all(rel_l1(u32, ur) < L1_SHOCKED), rel_l1(u32, ur)
 
@@ -212,7 +218,9 @@ def test_titarev_toro_steps(W, stream):
     u, t, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=300)
     ur, tr, takenr, _ = oracle.step(P, nsteps=300)
     assert taken == takenr == 300 and abs(t - tr) <= 1e-11 * tr
-    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=300)[0], P.u0, "titarev-toro 300 steps")
+    from parity import noisy_steps
+    check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=300)[0], P.u0, "titarev-toro 300 steps",
+            run_noisy=lambda: noisy_steps(P, 300))
     u32, _, _, _ = gpu_steps(W, stream, P, "f32", nsteps=300)
     assert np.all(rel_l1(u32, ur) < L1_SHOCKED), rel_l1(u32, ur)
 
@@ -224,7 +232,8 @@ def test_lax_steps(W, stream):
         u, _, taken, _ = gpu_steps(W, stream, P, "f64", nsteps=200, flux=flux)
         ur, _, takenr, _ = oracle.step(P, nsteps=200, flux=flux)
         assert taken == takenr == 200
-        check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=200, flux=flux)[0], P.u0, f"lax {flux} 200 steps")
+        check64(u, ur, lambda u0: oracle.step(P, u0, nsteps=200, flux=flux)[0], P.u0, f"lax {flux} 200 steps",
+                run_noisy=lambda: noisy_steps(P, 200, flux=flux))
 
 
 def test_2d_smooth_f32_l1(W, stream):

@@ -72,7 +72,7 @@ def test_weno_rhs_parity_f64(W, stream, name, make, params):
     prm = dict(WENO, **params)
     L, nonph = gpu_rhs(W, stream, P, "f64", **prm)
     Lr, _ = oracle.rhs(P, **prm)
-    check64(L, Lr, lambda u0: oracle.rhs(P, u0, **prm)[0], P.u0, name)
+    check64(L, Lr, lambda u0: oracle.rhs(P, u0, **prm)[0], P.u0, name, strict=True)
     assert nonph == 0
 
 
