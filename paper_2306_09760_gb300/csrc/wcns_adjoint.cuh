@@ -15,12 +15,11 @@
 
 namespace wcns {
 
-// d/dw of Eq. 20 for one weight: the map is w + 1/2 sum_j a_j(w) tanh(xi (w - n_j)) with
-// a_1 = c_1 - w, a_J = w - c_{J-1} and constant middle amplitudes.
+// tanh(z) in t and its derivative 1 - t^2 as the return value, with the exact select
+// where tanh rounds to +-1 (the derivative is then 0).
 template <typename T>
 WCNS_HD T tanh_sat_d(T z, T& t) {
-  T a = Num<T>::abs_(z);
-  if (a >= Num<T>::kSat) {
+  if (Num<T>::abs_(z) >= Num<T>::kSat) {
     t = z > T(0) ? T(1) : T(-1);
     return T(0);
   }
@@ -28,161 +27,173 @@ WCNS_HD T tanh_sat_d(T z, T& t) {
   return T(1) - t * t;
 }
 
-template <typename T>
-WCNS_HD T fe_map0_d(T w, const SchemeT<T>& s) {
-  const T xi = s.xi;
-  T t1, t2, t3;
-  T e1 = tanh_sat_d<T>(xi * (w - s.null0[0]), t1);
-  T e2 = tanh_sat_d<T>(xi * (w - s.null0[1]), t2);
-  T e3 = tanh_sat_d<T>(xi * (w - s.null0[2]), t3);
-  T acc = -t1 + (T(1.0 / 16.0) - w) * xi * e1;
-  acc = acc + T(1.0 / 6.0 - 1.0 / 16.0) * xi * e2;
-  acc = acc + t3 + (w - T(1.0 / 6.0)) * xi * e3;
-  return T(1) + acc / T(2);
-}
-template <typename T>
-WCNS_HD T fe_map1_d(T w, const SchemeT<T>& s) {
-  const T xi = s.xi;
-  T t1, t2, t3, t4;
-  T e1 = tanh_sat_d<T>(xi * (w - s.null1[0]), t1);
-  T e2 = tanh_sat_d<T>(xi * (w - s.null1[1]), t2);
-  T e3 = tanh_sat_d<T>(xi * (w - s.null1[2]), t3);
-  T e4 = tanh_sat_d<T>(xi * (w - s.null1[3]), t4);
-  T acc = -t1 + (T(10.0 / 16.0) - w) * xi * e1;
-  acc = acc + T(1.0 / 2.0 - 10.0 / 16.0) * xi * e2;
-  acc = acc + T(5.0 / 6.0 - 1.0 / 2.0) * xi * e3;
-  acc = acc + t4 + (w - T(5.0 / 6.0)) * xi * e4;
-  return T(1) + acc / T(2);
-}
-template <typename T>
-WCNS_HD T fe_map2_d(T w, const SchemeT<T>& s) {
-  const T xi = s.xi;
-  T t1, t2, t3;
-  T e1 = tanh_sat_d<T>(xi * (w - s.null2[0]), t1);
-  T e2 = tanh_sat_d<T>(xi * (w - s.null2[1]), t2);
-  T e3 = tanh_sat_d<T>(xi * (w - s.null2[2]), t3);
-  T acc = -t1 + (T(5.0 / 16.0) - w) * xi * e1;
-  acc = acc + T(1.0 / 2.0 - 5.0 / 16.0) * xi * e2;
-  acc = acc + t3 + (w - T(1.0 / 2.0)) * xi * e3;
-  return T(1) + acc / T(2);
+// Eq. 20 for one weight together with its derivative.  With amplitudes a_1 = (c_1 - w)/2,
+// a_j = (c_j - c_{j-1})/2 in the middle and a_J = (w - c_{J-1})/2 the map is
+//   g(w) = w + sum_j a_j tanh(xi (w - n_j)),
+// so g'(w) = 1 + (t_J - t_1)/2 + xi sum_j a_j (1 - t_j^2) with t_j the tanh terms.  Each
+// term is evaluated once and serves both.  The value is the forward map's (fe_map0..2):
+// the exponential form of tanh in single precision at moderate xi, otherwise tanh with
+// the exact select where it rounds to +-1 (there the term's derivative is 0; where every
+// term is saturated this is the forward map's staircase, with slope 0 or 1).
+template <typename T, int K>
+WCNS_HD T fe_map_vd(T w, const T (&n)[K], const T (&c)[K - 1], const SchemeT<T>& s, T& dg) {
+  T amp[K];
+  amp[0] = (c[0] - w) / T(2);
+#pragma unroll
+  for (int j = 1; j < K - 1; ++j) amp[j] = (c[j] - c[j - 1]) / T(2);
+  amp[K - 1] = (w - c[K - 2]) / T(2);
+  bool expf_form = false;
+  if constexpr (sizeof(T) == 4) expf_form = s.xi_small != 0;
+  T acc = T(0), dacc = T(0), t_first = T(0), t_last = T(0);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const T z = s.xi * (w - n[j]);
+    T t, e;
+    if constexpr (sizeof(T) == 4) {
+      if (expf_form) {
+        t = tanh_expf(z);
+        e = T(1) - t * t;
+      } else {
+        e = tanh_sat_d<T>(z, t);
+      }
+    } else {
+      e = tanh_sat_d<T>(z, t);
+    }
+    acc = acc + amp[j] * t;
+    dacc = dacc + amp[j] * e;
+    if (j == 0) t_first = t;
+    if (j == K - 1) t_last = t;
+  }
+  dg = T(1) + (t_last - t_first) / T(2) + s.xi * dacc;
+  return acc + w;
 }
 
-// Reverse of weno_side: given the cotangent gv of the interpolated value, adds the
-// cotangents of the five inputs to dv[0..4].
+// One-sided interpolation and its gradient: the value of weno_side (WCNS family; JS,
+// Z with p = 1 or 2, FE and PFE weights, with or without renormalisation) from the five
+// inputs v, and d(value)/d v_m in gr[m].  Forward: Eq. 5 values, Eq. 9-10 indicators,
+// Eq. 11 or Eq. 14-15 weights, the App. A box, the Eq. 20 map and its renormalisation,
+// the Eq. 6 combination, with the forward's ideal-plateau tests (where they hold the
+// weights are the ideal ones and the map is flat, so only the Eq. 5 values carry
+// derivatives).  Reverse: the same steps backwards from a unit seed on the value.
 template <typename T>
-WCNS_HD void weno_side_vjp(const T (&v)[5], T gv, const SchemeT<T>& s, T (&dv)[5]) {
+WCNS_HD T weno_side_grad(const T (&v)[5], const SchemeT<T>& s, T (&gr)[5]) {
   const T d[3] = {T(1.0 / 16.0), T(10.0 / 16.0), T(5.0 / 16.0)};
   // ---- forward, keeping what the reverse needs
   T q[3], f[3], sm[3], IS[3];
-  q[0] = (T(3) * v[0] - T(10) * v[1] + T(15) * v[2]) / T(8);
-  q[1] = (-v[1] + T(6) * v[2] + T(3) * v[3]) / T(8);
-  q[2] = (T(3) * v[2] + T(6) * v[3] - v[4]) / T(8);
+  q[0] = T(0.375) * v[0] - T(1.25) * v[1] + T(1.875) * v[2];
+  q[1] = -T(0.125) * v[1] + T(0.75) * v[2] + T(0.375) * v[3];
+  q[2] = T(0.375) * v[2] + T(0.75) * v[3] - T(0.125) * v[4];
   f[0] = (v[0] - T(4) * v[1] + T(3) * v[2]) / T(2); sm[0] = v[0] - T(2) * v[1] + v[2];
   f[1] = (v[3] - v[1]) / T(2);                      sm[1] = v[1] - T(2) * v[2] + v[3];
   f[2] = (T(-3) * v[2] + T(4) * v[3] - v[4]) / T(2); sm[2] = v[2] - T(2) * v[3] + v[4];
-  #pragma unroll
+#pragma unroll
   for (int k = 0; k < 3; ++k) IS[k] = f[k] * f[k] + sm[k] * sm[k];
   const T eps = s.eps;
-  T w[3], om[3], alpha[3], A = T(0), r[3] = {T(0), T(0), T(0)}, tau = T(0), sgn = T(0);
-  T G = T(1);
-  bool mapped = false;
   const bool js = (s.weights == 0);
+  T b[3], om[3], alpha[3], r[3] = {T(0), T(0), T(0)}, inv[3] = {T(0), T(0), T(0)};
+  T A = T(0), sgn = T(0), tau = T(0);
+  bool plateau = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) b[k] = IS[k] + eps;
   if (js) {
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      T b = IS[k] + eps;
-      alpha[k] = d[k] / (b * b);
+      alpha[k] = Num<T>::div_(d[k], b[k] * b[k]);
       A = A + alpha[k];
     }
   } else {
-    T diff = IS[0] - IS[2];
+    const T diff = IS[0] - IS[2];
     tau = Num<T>::abs_(diff);
     sgn = diff > T(0) ? T(1) : (diff < T(0) ? T(-1) : T(0));
-    #pragma unroll
+    bool small = s.weights == 2;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      r[k] = tau / (IS[k] + eps);
-      T rp = (s.zp == 2) ? r[k] * r[k] : r[k];
+      inv[k] = Num<T>::rcp_(b[k]);
+      r[k] = Num<T>::z_ratio(tau, b[k]);
+      const T rp = (s.zp == 2) ? r[k] * r[k] : r[k];
+      small = small && rp < s.ideal_ratio;
       alpha[k] = d[k] * (T(1) + rp);
       A = A + alpha[k];
     }
+    plateau = small;
   }
-  #pragma unroll
-  for (int k = 0; k < 3; ++k) om[k] = alpha[k] / A;
-  T g[3] = {om[0], om[1], om[2]};
-  if (s.weights == 2 || s.weights == 3) {
+  const T iA = Num<T>::rcp_(A);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) om[k] = alpha[k] * iA;
+  if (s.weights == 2 && s.ideal_margin[0] > T(0) && Num<T>::abs_(om[0] - d[0]) < s.ideal_margin[0] &&
+      Num<T>::abs_(om[1] - d[1]) < s.ideal_margin[1] && Num<T>::abs_(om[2] - d[2]) < s.ideal_margin[2])
+    plateau = true;
+  T w[3] = {om[0], om[1], om[2]}, dg[3] = {T(1), T(1), T(1)}, iG = T(1);
+  bool mapped = false;
+  if (plateau) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = d[k];
+  } else if (s.weights == 2 || s.weights == 3) {
     bool keep = false;
     if (s.weights == 3) {
       keep = true;
-      #pragma unroll
+#pragma unroll
       for (int k = 0; k < 3; ++k) keep = keep && (om[k] >= d[k] - s.cv) && (om[k] <= d[k] + s.cv);
     }
     if (!keep) {
       mapped = true;
-      g[0] = fe_map0<T>(om[0], s);
-      g[1] = fe_map1<T>(om[1], s);
-      g[2] = fe_map2<T>(om[2], s);
+      w[0] = fe_map_vd<T, 3>(om[0], s.null0, s.ctrl0, s, dg[0]);
+      w[1] = fe_map_vd<T, 4>(om[1], s.null1, s.ctrl1, s, dg[1]);
+      w[2] = fe_map_vd<T, 3>(om[2], s.null2, s.ctrl2, s, dg[2]);
+      if (s.renorm) {
+        iG = Num<T>::rcp_(w[0] + w[1] + w[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) w[k] = w[k] * iG;
+      }
     }
   }
-  if (mapped && s.renorm) {
-    G = g[0] + g[1] + g[2];
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) w[k] = g[k] / G;
-  } else {
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) w[k] = g[k];
-  }
-  // ---- reverse
-  T qb[3], wb[3];
-  #pragma unroll
-  for (int k = 0; k < 3; ++k) { wb[k] = gv * q[k]; qb[k] = gv * w[k]; }
-  T gb[3];
-  if (mapped && s.renorm) {
-    T dotw = wb[0] * w[0] + wb[1] * w[1] + wb[2] * w[2];
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) gb[k] = (wb[k] - dotw) / G;
-  } else {
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) gb[k] = wb[k];
-  }
-  T omb[3];
-  if (mapped) {
-    omb[0] = gb[0] * fe_map0_d<T>(om[0], s);
-    omb[1] = gb[1] * fe_map1_d<T>(om[1], s);
-    omb[2] = gb[2] * fe_map2_d<T>(om[2], s);
-  } else {
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) omb[k] = gb[k];
-  }
-  T doto = omb[0] * om[0] + omb[1] * om[1] + omb[2] * om[2];
-  T ab[3];
-  #pragma unroll
-  for (int k = 0; k < 3; ++k) ab[k] = (omb[k] - doto) / A;
+  const T value = w[0] * q[0] + w[1] * q[1] + w[2] * q[2];
+  // ---- reverse from a unit seed: qb = w, wb = q
   T ISb[3] = {T(0), T(0), T(0)};
-  if (js) {
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) ISb[k] = T(-2) * ab[k] * alpha[k] / (IS[k] + eps);
-  } else {
-    T taub = T(0);
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      T rpb = ab[k] * d[k];
-      T rb = (s.zp == 2) ? rpb * T(2) * r[k] : rpb;
-      T inv = T(1) / (IS[k] + eps);
-      taub = taub + rb * inv;
-      ISb[k] = ISb[k] - rb * r[k] * inv;
+  if (!plateau) {
+    T gb[3];
+    if (mapped && s.renorm) {
+      const T dotw = q[0] * w[0] + q[1] * w[1] + q[2] * w[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gb[k] = (q[k] - dotw) * iG;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gb[k] = q[k];
     }
-    ISb[0] = ISb[0] + taub * sgn;
-    ISb[2] = ISb[2] - taub * sgn;
+    T omb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) omb[k] = mapped ? gb[k] * dg[k] : gb[k];
+    const T doto = omb[0] * om[0] + omb[1] * om[1] + omb[2] * om[2];
+    T ab[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ab[k] = (omb[k] - doto) * iA;
+    if (js) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ISb[k] = Num<T>::div_(T(-2) * ab[k] * alpha[k], b[k]);
+    } else {
+      T taub = T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const T rpb = ab[k] * d[k];
+        const T rb = (s.zp == 2) ? rpb * T(2) * r[k] : rpb;
+        taub = taub + rb * inv[k];
+        ISb[k] = -rb * r[k] * inv[k];
+      }
+      ISb[0] = ISb[0] + taub * sgn;
+      ISb[2] = ISb[2] - taub * sgn;
+    }
   }
+  const T qb0 = w[0], qb1 = w[1], qb2 = w[2];
   T fb[3], sb[3];
-  #pragma unroll
+#pragma unroll
   for (int k = 0; k < 3; ++k) { fb[k] = T(2) * f[k] * ISb[k]; sb[k] = T(2) * sm[k] * ISb[k]; }
-  dv[0] = dv[0] + T(3.0 / 8.0) * qb[0] + T(0.5) * fb[0] + sb[0];
-  dv[1] = dv[1] - T(10.0 / 8.0) * qb[0] - T(1.0 / 8.0) * qb[1] - T(2) * fb[0] - T(2) * sb[0] - T(0.5) * fb[1] + sb[1];
-  dv[2] = dv[2] + T(15.0 / 8.0) * qb[0] + T(6.0 / 8.0) * qb[1] + T(3.0 / 8.0) * qb[2] + T(1.5) * fb[0] + sb[0] -
-          T(2) * sb[1] - T(1.5) * fb[2] + sb[2];
-  dv[3] = dv[3] + T(3.0 / 8.0) * qb[1] + T(6.0 / 8.0) * qb[2] + T(0.5) * fb[1] + sb[1] + T(2) * fb[2] - T(2) * sb[2];
-  dv[4] = dv[4] - T(1.0 / 8.0) * qb[2] - T(0.5) * fb[2] + sb[2];
+  gr[0] = T(3.0 / 8.0) * qb0 + T(0.5) * fb[0] + sb[0];
+  gr[1] = -T(10.0 / 8.0) * qb0 - T(1.0 / 8.0) * qb1 - T(2) * fb[0] - T(2) * sb[0] - T(0.5) * fb[1] + sb[1];
+  gr[2] = T(15.0 / 8.0) * qb0 + T(6.0 / 8.0) * qb1 + T(3.0 / 8.0) * qb2 + T(1.5) * fb[0] + sb[0] - T(2) * sb[1] -
+          T(1.5) * fb[2] + sb[2];
+  gr[3] = T(3.0 / 8.0) * qb1 + T(6.0 / 8.0) * qb2 + T(0.5) * fb[1] + sb[1] + T(2) * fb[2] - T(2) * sb[2];
+  gr[4] = -T(1.0 / 8.0) * qb2 - T(0.5) * fb[2] + sb[2];
+  return value;
 }
 
 // Reverse of the physical flux F(U) in the sweep normal: adds (dF/dU)^T Fb to Ub.
@@ -343,7 +354,10 @@ WCNS_HD void roe_basis_vjp(const T (&Ua)[NV], const T (&Ub_)[NV], T gm1, const B
   prim_vjp(Ub_, b, sb, ubb, vbb, Hbb, sbb, Sb);
 }
 
-// Reverse of interface_flux for LLF_FROZEN: Sb[m][k] += d(F . Fb)/d S[m][k].
+// Reverse of interface_flux for LLF_FROZEN: Sb[m][k] += d(F . Fb)/d S[m][k].  The forward
+// pass keeps, for each field and side, the gradient of the interpolated value with
+// respect to its five inputs (weno_side_grad), so the reverse needs no second pass
+// through the weights.
 template <typename T, int NV>
 WCNS_HD void interface_flux_vjp(const T (&S)[6][NV], const SchemeT<T>& s, int dir, const T (&Fb)[NV],
                                 T (&Sb)[6][NV]) {
@@ -353,39 +367,44 @@ WCNS_HD void interface_flux_vjp(const T (&S)[6][NV], const SchemeT<T>& s, int di
   T UL[NV], UR[NV];
   CharBasis<T, NV> cb{};
   T WL[NV], WR[NV];
+  T gL[NV][5], gR[NV][5];  // gL[k][m]: d WL_k / d v_m (v = cells i-2..i+2); gR: mirrored cells i+3..i-1
   const bool ch = s.characteristic != 0;
   if (ch) {
     T Ui[NV], Uj[NV];
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < NV; ++k) { Ui[k] = S[2][k]; Uj[k] = S[3][k]; }
     EulerState<T, NV> a = euler_prim<T, NV>(Ui, gm1), b = euler_prim<T, NV>(Uj, gm1);
     RoeAvg<T, NV> r = roe_avg<T, NV>(a, b, gm1);
     cb = char_basis<T, NV>(r, gm1);
     T W[6][NV];
-    #pragma unroll
+#pragma unroll
     for (int m = 0; m < 6; ++m) char_project<T, NV>(cb, S[m], W[m]);
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < NV; ++k) {
-      WL[k] = weno_side<T, 0>(W[0][k], W[1][k], W[2][k], W[3][k], W[4][k], s);
-      WR[k] = weno_side<T, 0>(W[5][k], W[4][k], W[3][k], W[2][k], W[1][k], s);
+      const T vl[5] = {W[0][k], W[1][k], W[2][k], W[3][k], W[4][k]};
+      const T vr[5] = {W[5][k], W[4][k], W[3][k], W[2][k], W[1][k]};
+      WL[k] = weno_side_grad<T>(vl, s, gL[k]);
+      WR[k] = weno_side_grad<T>(vr, s, gR[k]);
     }
     char_unproject<T, NV>(cb, WL, UL);
     char_unproject<T, NV>(cb, WR, UR);
   } else {
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < NV; ++k) {
-      UL[k] = weno_side<T, 0>(S[0][k], S[1][k], S[2][k], S[3][k], S[4][k], s);
-      UR[k] = weno_side<T, 0>(S[5][k], S[4][k], S[3][k], S[2][k], S[1][k], s);
+      const T vl[5] = {S[0][k], S[1][k], S[2][k], S[3][k], S[4][k]};
+      const T vr[5] = {S[5][k], S[4][k], S[3][k], S[2][k], S[1][k]};
+      UL[k] = weno_side_grad<T>(vl, s, gL[k]);
+      UR[k] = weno_side_grad<T>(vr, s, gR[k]);
     }
   }
   const bool fallback = !physical<T, NV>(UL, gm1) || !physical<T, NV>(UR, gm1);
   if (fallback) {
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < NV; ++k) { UL[k] = S[2][k]; UR[k] = S[3][k]; }
   }
   // ---- reverse of F = (F(UL) + F(UR))/2 - alpha (UR - UL)/2
   T ULb[NV], URb[NV], half[NV];
-  #pragma unroll
+#pragma unroll
   for (int k = 0; k < NV; ++k) {
     half[k] = T(0.5) * Fb[k];
     ULb[k] = T(0.5) * alpha * Fb[k];
@@ -394,56 +413,36 @@ WCNS_HD void interface_flux_vjp(const T (&S)[6][NV], const SchemeT<T>& s, int di
   euler_flux_vjp<T, NV>(UL, gm1, half, ULb);
   euler_flux_vjp<T, NV>(UR, gm1, half, URb);
   if (fallback) {
-    #pragma unroll
+#pragma unroll
     for (int k = 0; k < NV; ++k) { Sb[2][k] = Sb[2][k] + ULb[k]; Sb[3][k] = Sb[3][k] + URb[k]; }
     return;
   }
   if (!ch) {
-    #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      T dv[5] = {T(0), T(0), T(0), T(0), T(0)};
-      T v[5] = {S[0][k], S[1][k], S[2][k], S[3][k], S[4][k]};
-      weno_side_vjp<T>(v, ULb[k], s, dv);
-      #pragma unroll
-      for (int m = 0; m < 5; ++m) Sb[m][k] = Sb[m][k] + dv[m];
-      T dw[5] = {T(0), T(0), T(0), T(0), T(0)};
-      T w[5] = {S[5][k], S[4][k], S[3][k], S[2][k], S[1][k]};
-      weno_side_vjp<T>(w, URb[k], s, dw);
-      #pragma unroll
-      for (int m = 0; m < 5; ++m) Sb[5 - m][k] = Sb[5 - m][k] + dw[m];
-    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        Sb[m][k] = Sb[m][k] + ULb[k] * gL[k][m];
+        Sb[5 - m][k] = Sb[5 - m][k] + URb[k] * gR[k][m];
+      }
     return;
   }
   BasisBar<T> bb{T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   T WLb[NV], WRb[NV];
   char_unproject_vjp<T, NV>(cb, WL, ULb, WLb, bb);
   char_unproject_vjp<T, NV>(cb, WR, URb, WRb, bb);
-  // recompute the projected stencil (cheaper than keeping it live)
-  T W[6][NV];
-  #pragma unroll
-  for (int m = 0; m < 6; ++m) char_project<T, NV>(cb, S[m], W[m]);
   T Wb[6][NV];
-  #pragma unroll
-  for (int m = 0; m < 6; ++m)
-    #pragma unroll
-    for (int k = 0; k < NV; ++k) Wb[m][k] = T(0);
-  #pragma unroll
+#pragma unroll
   for (int k = 0; k < NV; ++k) {
-    T dv[5] = {T(0), T(0), T(0), T(0), T(0)};
-    T v[5] = {W[0][k], W[1][k], W[2][k], W[3][k], W[4][k]};
-    weno_side_vjp<T>(v, WLb[k], s, dv);
-    #pragma unroll
-    for (int m = 0; m < 5; ++m) Wb[m][k] = Wb[m][k] + dv[m];
-    T dw[5] = {T(0), T(0), T(0), T(0), T(0)};
-    T w[5] = {W[5][k], W[4][k], W[3][k], W[2][k], W[1][k]};
-    weno_side_vjp<T>(w, WRb[k], s, dw);
-    #pragma unroll
-    for (int m = 0; m < 5; ++m) Wb[5 - m][k] = Wb[5 - m][k] + dw[m];
+    Wb[0][k] = WLb[k] * gL[k][0];
+    Wb[5][k] = WRb[k] * gR[k][0];
+#pragma unroll
+    for (int m = 1; m < 5; ++m) Wb[m][k] = WLb[k] * gL[k][m] + WRb[k] * gR[k][5 - m];
   }
-  #pragma unroll
+#pragma unroll
   for (int m = 0; m < 6; ++m) char_project_vjp<T, NV>(cb, S[m], Wb[m], Sb[m], bb);
   T Ui[NV], Uj[NV];
-  #pragma unroll
+#pragma unroll
   for (int k = 0; k < NV; ++k) { Ui[k] = S[2][k]; Uj[k] = S[3][k]; }
   roe_basis_vjp<T, NV>(Ui, Uj, gm1, bb, Sb[2], Sb[3]);
 }
