@@ -116,7 +116,7 @@ class ClockSampler:
 
 # The sources of the sweep and CFL kernels' code: device numerics, the packed
 # single-precision interface flux, and the kernel bodies.
-SWEEP_SOURCES = ("wcns_device.cuh", "wcns_pair.cuh", "wcns_kernels.cuh")
+SWEEP_SOURCES = ("wcns_device.cuh", "wcns_pair.cuh", "wcns_kernels.cuh", "wcns_band.cuh")
 
 
 def kernel_source_digest(read=None):
@@ -276,15 +276,18 @@ def time_solver(W, torch, S, stream, steps, warmup, profile=True):
     return ms, prof
 
 
-def measure_line(W, torch, inputs, dtype, steps, warmup, local, barrier, e2e_steps=10):
+def measure_line(W, torch, inputs, dtype, steps, warmup, local, barrier, e2e_steps=10, banded=False):
     """Device-resident timing of `steps` RK3 steps of the 2048^2 workload in `dtype`,
     per-kernel event times, clocks during the timed region, and the end-to-end rate
-    through wcns_step_host on a pinned host buffer (copies inside the timed region)."""
+    through wcns_step_host on a pinned host buffer (copies inside the timed region).
+    banded: the stages run in the banded form (wcns_set_stage_form)."""
     P = inputs.riemann2d(N_MAIN, seed=SEED)
     tdtype = torch.float32 if dtype == "f32" else torch.float64
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         S = W.Solver(P, dtype, stream=stream)
+        if banded:
+            W.wcns_set_stage_form(S.ctx, True)
         S.step(0.0, warmup)
         torch.cuda.synchronize()
         W.wcns_profile_enable(S.ctx, True)
@@ -329,8 +332,10 @@ def roofline_of(prof, ncell, dtype, alu_peak, alu_src):
     dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
     launches, tot_ms = prof[dom]
     per_dir = flops_per_cell_rhs() / 2.0
-    stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0}.get(dom, 0)
-    flops_per_launch = ncell * (per_dir + stage_extra)
+    # the banded stage evaluates both directions and the stage update in one launch
+    dirs = 2 if dom == "stage_band_2d" else 1
+    stage_extra = {"sweep_y_stage_2d": 5 * 4, "sweep_x_lx_2d": 0, "stage_band_2d": 5 * 4}.get(dom, 0)
+    flops_per_launch = ncell * (dirs * per_dir + stage_extra)
     achieved = flops_per_launch / (tot_ms / launches / 1e3) / 1e12
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved / alu_peak, "traffic": ncu_traffic(dom) if dtype == "f32" else None,
@@ -377,7 +382,8 @@ def run_ours(args):
             dist.barrier()
 
     dtype = args.dtype
-    m = measure_line(W, torch, inputs, dtype, args.steps, args.warmup, local, barrier)
+    banded = args.stage_form == "banded"
+    m = measure_line(W, torch, inputs, dtype, args.steps, args.warmup, local, barrier, banded=banded)
     P = m["P"]
     ncell = P.nx * P.ny
     ms_max, e2e_max = max_over_ranks([m["ms"], m["e2e_wall"]], world, device="cuda")
@@ -415,7 +421,8 @@ def run_ours(args):
         "dtype": dtype, "data": "synthetic",
         "config": {"workload": "2D Euler 2048x2048, four-quadrant Riemann data (seed 0, split x=y=0.8), "
                                "transmissive, CFL 0.5, WCNS-FE (xi=1e6, kappa=0.5), HLLC, characteristic; "
-                               + ("FP32 bulk" if dtype == "f32" else "FP64"),
+                               + ("FP32 bulk" if dtype == "f32" else "FP64")
+                               + ("; banded stage form" if banded else ""),
                    "global_batch": world, "seq_len": N_MAIN, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2: each stage touches 4 state-size arrays (256 MiB) > 126 MiB L2",
                    "simulated_time": m["t_sim"], "steps_taken": m["steps_taken"], "fallback_interfaces": m["nonph"]},
@@ -499,6 +506,10 @@ def run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, b
     except Exception as e:
         out["adjoint_vortex_512"] = {"error": repr(e)}
     try:
+        out["euler2d_2048_f32_banded"] = run_banded_variant(W, torch, inputs, stream)
+    except Exception as e:
+        out["euler2d_2048_f32_banded"] = {"error": repr(e)}
+    try:
         out["fp32_error"] = run_fp32_error(W, torch, inputs)
     except Exception as e:
         out["fp32_error"] = {"error": repr(e)}
@@ -518,6 +529,28 @@ def run_variants(args, W, torch, inputs, hbm_peak, fp64_peak, fp64_src, local, b
                      "hbm_frac": rate * 1e6 * nbytes / 1e9 / hbm_peak if ok else None,
                      "status": W.wcns_status_string(st), "steps_taken": taken}
     return out
+
+
+def run_banded_variant(W, torch, inputs, stream, steps=50, warm=3):
+    """The main workload with the banded stage form (wcns_set_stage_form): one persistent
+    launch per RK stage, partial stage in an L2-resident ring.  Rate, per-stage launch
+    time (library profiler) and the per-launch DRAM bytes of the committed ncu capture."""
+    P = inputs.riemann2d(N_MAIN, seed=SEED)
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, "f32", stream=stream)
+        W.wcns_set_stage_form(S.ctx, True)
+        ms, prof = time_solver(W, torch, S, stream, steps, warm, profile=True)
+        st, _ = S.status()
+        _, taken = S.time()
+        S.close()
+    ok = st == W.WCNS_OK and taken == steps + warm
+    rate = P.nx * P.ny * steps / (ms / 1e3) / 1e6
+    band = prof.get("stage_band_2d", (0, 0.0))
+    return {"value": rate if ok else None, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "stage_ms": band[1] / band[0] if band[0] else None,
+            "dram_bytes_per_stage": ncu_traffic("stage_band_2d"),
+            "algorithmic_bytes_per_stage": {"first": 2 * 4 * 4 * P.nx * P.ny, "later": 3 * 4 * 4 * P.nx * P.ny},
+            "status": W.wcns_status_string(st), "steps_taken": taken}
 
 
 def run_fp32_error(W, torch, inputs):
@@ -708,6 +741,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"],
                     help="element type of the main line (default f32: FP32 bulk arithmetic)")
+    ap.add_argument("--stage-form", default="two-launch", choices=["two-launch", "banded"],
+                    help="form of the 2D stages of the main line (wcns_set_stage_form; default: two launches)")
     ap.add_argument("--adjoint-kernels", type=int, default=0, metavar="STEPS",
                     help="only time STEPS FP32 adjoint steps of the adjoint workload per kernel (for profiling)")
     args = ap.parse_args()

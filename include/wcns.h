@@ -212,6 +212,31 @@ wcns_status wcns_weight_hist(wcns_ctx* ctx, const void* u, int32_t nbins, uint64
  * advection.  Captured step graphs are dropped (rebuilt on the next wcns_step). */
 wcns_status wcns_set_faces(wcns_ctx* ctx, const wcns_faces* faces);
 
+/* Chooses how the RK stages of a 2D Euler grid run (steps (a)-(e) and the stage update
+ * of wcns_step; the scheme itself, Eq. 2-3 with the TVD-RK3 or Eq. 16 stages, is the
+ * same either way, and so is every result, bit for bit).
+ *   banded = 0 (the default): an x-sweep launch over the whole grid, which writes the
+ *     partial stage into a state-sized buffer, then a y-sweep launch that completes it.
+ *   banded = 1: each stage is one cooperative persistent launch over bands of rows --
+ *     the x-direction interfaces of a band write its partial stage into one of four
+ *     band-sized ring slots, and the band's y-direction interfaces complete the stage
+ *     from it -- so the partial stage stays in L2 and each stage moves about its
+ *     algorithmic DRAM bytes (read u and u^n once, write the stage once) instead of about
+ *     twice that.  On GB300 the sweeps are bound by instruction issue, not by DRAM, and
+ *     the persistent loop's per-tile synchronisation costs more than the traffic saves
+ *     (2048^2: 0.32 ms against 0.24 ms per FP32 stage), hence not the default.  It
+ *     applies to 2D Euler grids of the default scheme configuration (FE weights with
+ *     the Table 2 rows at kappa = 0.5, xi >= 1e4, Z p = 1, renormalised, HLLC,
+ *     characteristic) with more than four bands of rows (bands are whole 75-row y
+ *     tiles, at least 150 rows, at most 64 bands), in single precision only on grids
+ *     wide enough for the four-interface x tiles.  The first banded = 1 call allocates
+ *     the ring (4 slots of 4 x band rows x pitch elements); make it before any stream
+ *     capture.
+ * Errors: WCNS_ERR_ARG (null context), WCNS_ERR_UNSUPPORTED (banded = 1 where it does
+ * not apply), WCNS_ERR_NOMEM.  Captured step graphs are dropped (rebuilt on the next
+ * wcns_step). */
+wcns_status wcns_set_stage_form(wcns_ctx* ctx, int32_t banded);
+
 /* The reductions of wcns_reduce (SUM, L1, LINF only) without a context and without
  * any device allocation.  The paper has no counterpart: this serves callers that
  * cannot call cudaMalloc where they need the reduction -- a loop that reserved all of
@@ -279,7 +304,7 @@ wcns_status wcns_profile_enable(wcns_ctx* ctx, int32_t on);
 
 /* Synchronises the stream and returns, per kernel kind, its name (48-byte slots in
  * `names`), launches and total milliseconds since the last read, then resets them.
- * max_entries must be >= 10 (the number of kinds); *n_entries receives that number. */
+ * max_entries must be >= 11 (the number of kinds); *n_entries receives that number. */
 wcns_status wcns_profile_read(wcns_ctx* ctx, int32_t max_entries, char* names, int64_t* launches,
                               double* ms, int32_t* n_entries);
 

@@ -35,12 +35,14 @@ UNITS = {
     "wcns_f64_x4.cu": [],
     "wcns_f64_y.cu": [],
     "wcns_f64_adj.cu": [],
+    "wcns_f64_band.cu": [],
     "wcns_f32.cu": FAST_F32,
     "wcns_f32_x1.cu": FAST_F32,
     "wcns_f32_x3.cu": FAST_F32,
     "wcns_f32_x4.cu": FAST_F32,
     "wcns_f32_y.cu": FAST_F32,
     "wcns_f32_adj.cu": FAST_F32,
+    "wcns_f32_band.cu": FAST_F32,
 }
 
 

@@ -26,6 +26,9 @@ struct wcns_ctx {
   void* u3;              // third stage state (RK4 only)
   void* R;               // L_x planes (2D)
   void* host_state;      // device copy used by wcns_step_host (lazy)
+  void* ring;            // partial-stage ring of the banded 2D stage (lazy, wcns_set_stage_form)
+  bool banded;           // stages run banded (wcns_set_stage_form)
+  unsigned* d_band;      // banded stage counters (kBandCounterWords, in scal)
   void* adj1;            // adjoint stage cotangents (lazy)
   void* adj2;
   // small device scalars (one allocation)
@@ -56,9 +59,10 @@ struct wcns_ctx {
 
 namespace {
 enum ProfKind { kProfSweepXRhs = 0, kProfSweepYRhs, kProfSweepXStage1D, kProfSweepXLx, kProfSweepYStage, kProfDt,
-                kProfReduce, kProfAdjX, kProfAdjY, kProfDtFused, kProfCount };
+                kProfReduce, kProfAdjX, kProfAdjY, kProfDtFused, kProfStageBand, kProfCount };
 const char* const kProfNames[kProfCount] = {"sweep_x_rhs", "sweep_y_rhs", "sweep_x_stage_1d", "sweep_x_lx_2d",
-                                            "sweep_y_stage_2d", "dt_cfl", "reduce", "adjoint_x", "adjoint_y", "dt_from_maxima"};
+                                            "sweep_y_stage_2d", "dt_cfl", "reduce", "adjoint_x", "adjoint_y", "dt_from_maxima",
+                                            "stage_band_2d"};
 }  // namespace
 
 namespace {
@@ -121,6 +125,11 @@ cudaError_t by_type(int dtype, F64 f64, F32 f32) {
   return dtype == WCNS_F64 ? f64() : f32();
 }
 
+bool by_type_bool(int dtype, bool f64, bool f32) { return dtype == WCNS_F64 ? f64 : f32; }
+
+// The banded stage's counters sit in the context's scalar block at byte 1024.
+static_assert(1024 + sizeof(unsigned) * kBandCounterWords <= 4096, "band counters fit the scalar block");
+
 // Runs `f` (one kernel launch), bracketed by events when per-kernel timing is on.
 template <class F>
 cudaError_t timed(wcns_ctx* c, int kind, F f) {
@@ -172,15 +181,13 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
                  [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
   }
   // 2D: the x sweep writes L_x (RHS) or the partial stage (all terms but the y part of L)
-  // into R (skipped when dt == 0), then the y sweep adds L_y or its stage multiple.
+  // into R (skipped when dt == 0), then the y sweep adds L_y or its stage multiple.  A
+  // stage on a grid with a partial-stage ring runs both sweeps in one banded launch.
   x.out = static_cast<T*>(c->R);
   x.dt = stage_mode ? c->d_dt : nullptr;
   x.un = static_cast<const T*>(un);
   x.a = k.a; x.b = k.b;
   x.stage = stage_mode;
-  cudaError_t e = timed(c, stage_mode ? kProfSweepXLx : kProfSweepXRhs,
-                        [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
-  if (e != cudaSuccess) return e;
   SweepCall<T> y{};
   y.u = static_cast<const T*>(u);
   y.un = static_cast<const T*>(un);
@@ -199,6 +206,13 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
     y.wave = c->d_wave;
     y.err = c->d_err;
   }
+  if (stage_mode && c->banded)
+    return timed(c, kProfStageBand, [&] {
+      return launch_stage_band<T>(c->gi, c->s, x, y, static_cast<T*>(c->ring), c->d_band, c->d_err, c->stream);
+    });
+  cudaError_t e = timed(c, stage_mode ? kProfSweepXLx : kProfSweepXRhs,
+                        [&] { return launch_sweep_x<T>(c->gi, c->s, x, c->stream); });
+  if (e != cudaSuccess) return e;
   return timed(c, stage_mode ? kProfSweepYStage : kProfSweepYRhs,
                [&] { return launch_sweep_y<T>(c->gi, c->s, y, c->stream); });
 }
@@ -517,6 +531,8 @@ wcns_status wcns_init(const wcns_grid* grid, const wcns_params* params, void* st
   c->d_counters = reinterpret_cast<unsigned int*>(b + 64);
   c->d_out = reinterpret_cast<double*>(b + 128);
   c->d_partials = reinterpret_cast<double*>(b + 4096);
+  c->d_band = reinterpret_cast<unsigned*>(b + 1024);  // kBandCounterWords (zeroed above)
+  c->banded = false;
   *out = c;
   return WCNS_OK;
 }
@@ -667,6 +683,18 @@ wcns_status wcns_set_faces(wcns_ctx* c, const wcns_faces* f) {
   return WCNS_OK;
 }
 
+wcns_status wcns_set_stage_form(wcns_ctx* c, int32_t banded) {
+  if (!c) return WCNS_ERR_ARG;
+  if (banded) {
+    if (!by_type_bool(c->g.dtype, band_applies<double>(c->gi, c->s), band_applies<float>(c->gi, c->s)))
+      return WCNS_ERR_UNSUPPORTED;
+    if (!c->ring) WCNS_TRY(cudaMalloc(&c->ring, band_ring_bytes_of(c->gi, c->elem)));
+  }
+  if (c->banded != (banded != 0)) drop_graph(c);  // captured steps hold the other form
+  c->banded = banded != 0;
+  return WCNS_OK;
+}
+
 wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const void* lam_np1, void* lam_n) {
   if (!c || !u_n || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(lam_np1) || !aligned16(lam_n))
     return WCNS_ERR_ARG;
@@ -763,6 +791,7 @@ void wcns_destroy(wcns_ctx* c) {
   if (c->u2) cudaFree(c->u2);
   if (c->u3) cudaFree(c->u3);
   if (c->R) cudaFree(c->R);
+  if (c->ring) cudaFree(c->ring);
   if (c->host_state) cudaFree(c->host_state);
   if (c->adj1) cudaFree(c->adj1);
   if (c->adj2) cudaFree(c->adj2);

@@ -973,20 +973,35 @@ WCNS_HD bool interface_flux(const T (&S)[6][NV], const SchemeT<T>& s, int dir, T
 
 // Eq. 3: -(1/h) sum_m d_m (F_{i+m-1/2} - F_{i-m+1/2}) from the six interface fluxes
 // f[0..5] = F_{i-5/2} .. F_{i+5/2}.
+// a * b + c, a * b and a + b of the Eq. 3 difference and the stage updates.  In single
+// precision they are explicitly rounded (one rounding for a * b + c): no compiler pass
+// may fuse or split them, so these expressions round the same way in every kernel they
+// are inlined into -- the banded stage kernel and the separate x- and y-sweep kernels
+// give the same single-precision states bit for bit.  In double precision they are the
+// plain expressions, which both forms compile alike (checked bit for bit as well).
+template <typename T> WCNS_HD T sfma(T a, T b, T c) { return a * b + c; }
+template <typename T> WCNS_HD T smul(T a, T b) { return a * b; }
+template <typename T> WCNS_HD T sadd(T a, T b) { return a + b; }
+#ifdef __CUDA_ARCH__
+template <> WCNS_HD float sfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> WCNS_HD float smul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> WCNS_HD float sadd<float>(float a, float b) { return __fadd_rn(a, b); }
+#endif
+
 template <typename T>
 WCNS_HD T flux_difference(T f0, T f1, T f2, T f3, T f4, T f5, T inv_h) {
   const T d1 = T(75.0 / 64.0), d2 = T(-25.0 / 384.0), d3 = T(3.0 / 640.0);
-  T acc = d1 * (f3 - f2);
-  acc = acc + d2 * (f4 - f1);
-  acc = acc + d3 * (f5 - f0);
-  return -(acc * inv_h);
+  T acc = smul<T>(d1, f3 - f2);
+  acc = sfma<T>(d2, f4 - f1, acc);
+  acc = sfma<T>(d3, f5 - f0, acc);
+  return -smul<T>(acc, inv_h);
 }
 
 // Spatial derivative from the six interface fluxes f[0..5] = F_{i-5/2} .. F_{i+5/2}:
 // Eq. 3 for the WCNS family, -(F_{i+1/2} - F_{i-1/2}) / h for the WENO family (App. B).
 template <typename T>
 WCNS_HD T flux_difference_family(int family, T f0, T f1, T f2, T f3, T f4, T f5, T inv_h) {
-  if (family == 1) return -((f3 - f2) * inv_h);
+  if (family == 1) return -smul<T>(f3 - f2, inv_h);
   return flux_difference<T>(f0, f1, f2, f3, f4, f5, inv_h);
 }
 

@@ -53,6 +53,18 @@ cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T
 template <typename T>
 cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);
 
+// One 2D Euler stage (the x and y sweep calls of a stage) as a single banded persistent
+// launch whose partial stage lives in a ring of band-sized slots (wcns_band.cuh).
+// band_applies: whether the banded form can run this grid and scheme; ring bytes from
+// band_ring_bytes_of; ctr: kBandCounterWords zeroed words.
+template <typename T>
+bool band_applies(const GridInfo& g, const Scheme& s);
+template <typename T>
+cudaError_t launch_stage_band(const GridInfo& g, const Scheme& s, const SweepCall<T>& x, const SweepCall<T>& y,
+                              T* ring, unsigned* ctr, int* err, cudaStream_t st);
+size_t band_ring_bytes_of(const GridInfo& g, size_t elem);
+constexpr int kBandCounterWords = 2 + 2 * 64;
+
 // Adjoint sweep: out = c1*X1 + c2*X2 + b*(mu + dt*(R + J^T mu)) (combine) or
 // out = J^T mu (x part of a 2D grid, combine == false).
 template <typename T>

@@ -64,9 +64,12 @@ __device__ __forceinline__ double sweep_time(const SweepArgs<T>& A) {
 // then adds b*dt*L_y, so its epilogue reads one array instead of two.
 enum SweepMode { kWriteL = 0, kStage = 1 };
 
+// Adds the warp's count of true flags to *ctr (one atomic per warp, by its first flagged lane).
 __device__ __forceinline__ void count_fallbacks(bool fb, unsigned long long* ctr) {
   unsigned m = __ballot_sync(0xffffffffu, fb);
-  if (m && (threadIdx.x & 31) == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
+  unsigned lane;
+  asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+  if (m && lane == ((unsigned)__ffs(m) - 1)) atomicAdd(ctr, (unsigned long long)__popc(m));
 }
 
 // Signal speeds |u| + c and |v| + c of one cell (rho, rho u, rho v, E) in the state's own
@@ -88,7 +91,8 @@ __device__ __forceinline__ bool cell_wave(T rho, T mu, T mv, T E, T g, T gm1, T&
 // nothing to add pass 0) merged into one of kWaveSlots slot pairs of wave with
 // atomicMax, and the warp's non-physical flag into *err.
 template <typename T>
-__device__ __forceinline__ void warp_wave(T mx, T my, bool bad, unsigned long long* wave, int* err) {
+__device__ __forceinline__ void warp_wave(T mx, T my, bool bad, unsigned vblock, unsigned long long* wave,
+                                          int* err) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -97,7 +101,7 @@ __device__ __forceinline__ void warp_wave(T mx, T my, bool bad, unsigned long lo
   const bool anybad = __any_sync(0xffffffffu, bad);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if ((tid & 31) == 0) {
-    const unsigned slot = (((unsigned)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y / 32) +
+    const unsigned slot = (vblock * (blockDim.x * blockDim.y / 32) +
                            (unsigned)(tid >> 5)) % kWaveSlots;
     atomicMax(&wave[2 * slot], (unsigned long long)__double_as_longlong((double)mx));
     atomicMax(&wave[2 * slot + 1], (unsigned long long)__double_as_longlong((double)my));
@@ -137,10 +141,14 @@ constexpr size_t sweep_x_smem() {
 template <typename T>
 constexpr int sweep_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
 
+// One x tile (row `row`, tile `tile` of the row) of the sweep; the block calls it
+// together.  The result goes to out[k * ostride + (row - orow0) * pitch + c] (the grid's
+// own layout when ostride = fstride and orow0 = 0; a band of rows of the partial-stage
+// ring otherwise).
 template <typename T, int NV, int MODE, int FIX, int P, int TH = kXThreads>
-__global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
+__device__ __forceinline__ void sweep_x_body(const SweepArgs<T>& A, int64_t row, int64_t tile, T* out,
+                                             int64_t ostride, int64_t orow0, unsigned char* smem_raw) {
   constexpr int IFC = sweep_x_ifc<P, TH>(), TILE = sweep_x_tile<P, TH>(), CELLS = sweep_x_cells<P, TH>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][CELLS]
   T* sf = su + NV * CELLS;                  // [NV][IFC]
   T* sn = sf + NV * IFC;                    // [NV][TILE] u^n (P > 1)
@@ -149,8 +157,7 @@ __global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(Swee
     if (A.dt->zero) return;  // the run has reached t_end: the step changes nothing
     dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
-  const int64_t row = A.row_major ? blockIdx.x : blockIdx.y;
-  const int64_t c0 = (int64_t)(A.row_major ? blockIdx.y : blockIdx.x) * TILE;
+  const int64_t c0 = tile * TILE;
   const int ntile = (int)min((int64_t)TILE, A.nx - c0);
   const T* base = A.u + row * A.pitch;
   const bool use_un = MODE == kStage && A.a != T(0);
@@ -213,29 +220,49 @@ __global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(Swee
     const int t = threadIdx.x + TH * q;
     if (t >= ntile) break;
     const int64_t off = row * A.pitch + c0 + t;
+    T* ob = out + (row - orow0) * A.pitch + c0 + t;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const T* f = sf + k * IFC + t;
       T L = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[1], f[2], f[3], f[4], f[5], A.inv_h);
       if (MODE == kWriteL) {
-        A.out[k * A.fstride + off] = L;
+        ob[k * ostride] = L;
       } else {
         const T cur = su[k * CELLS + t + 5];
         // u^n is staged only when it enters (a != 0); the general form multiplies by a
         const T unk = (P == 1) ? unv[k] : (use_un ? sn[k * TILE + t] : T(0));
         T v;
-        if (!A.general) {
-          v = A.b * (cur + dt * L);
-          if (A.a != T(0)) v = A.a * unk + v;
+        if constexpr (sizeof(T) == 4) {
+          if (!A.general) {
+            v = smul<T>(A.b, sfma<T>(dt, L, cur));
+            if (A.a != T(0)) v = sfma<T>(A.a, unk, v);
+          } else {
+            v = sfma<T>(smul<T>(A.e, dt), L, sfma<T>(A.a, unk, smul<T>(A.b, cur)));
+            if (A.X1) v = sfma<T>(A.c1, A.X1[k * A.fstride + off], v);
+            if (A.X2) v = sfma<T>(A.c2, A.X2[k * A.fstride + off], v);
+          }
         } else {
-          v = A.a * unk + A.b * cur + (A.e * dt) * L;
-          if (A.X1) v = v + A.c1 * A.X1[k * A.fstride + off];
-          if (A.X2) v = v + A.c2 * A.X2[k * A.fstride + off];
+          if (!A.general) {
+            v = A.b * (cur + dt * L);
+            if (A.a != T(0)) v = A.a * unk + v;
+          } else {
+            v = A.a * unk + A.b * cur + (A.e * dt) * L;
+            if (A.X1) v = v + A.c1 * A.X1[k * A.fstride + off];
+            if (A.X2) v = v + A.c2 * A.X2[k * A.fstride + off];
+          }
         }
-        A.out[k * A.fstride + off] = v;
+        ob[k * ostride] = v;
       }
     }
   }
+}
+
+template <typename T, int NV, int MODE, int FIX, int P, int TH = kXThreads>
+__global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t row = A.row_major ? blockIdx.x : blockIdx.y;
+  const int64_t tile = A.row_major ? blockIdx.y : blockIdx.x;
+  sweep_x_body<T, NV, MODE, FIX, P, TH>(A, row, tile, A.out, A.fstride, 0, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -256,9 +283,14 @@ constexpr int kYCells = kYIfc + 5;         // 85 staged rows
 template <typename T, int NV>
 constexpr size_t sweep_y_smem() { return sizeof(T) * NV * (kYCells + kYIfc) * kYCols; }
 
+// One y tile (column block bx, row block by) of the sweep; the block (kYCols x kYRowsT
+// threads) calls it together.  R is read at R[k * rstride + (r - rrow0) * pitch + c], with
+// loads that bypass L1 (R may have been written by other blocks of the same launch).
+// vblock spreads the fused CFL maxima over the slots.
 template <typename T, int NV, int MODE, int FIX>
-__global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep_y_kernel(SweepArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void sweep_y_body(const SweepArgs<T>& A, int64_t bx, int64_t by, const T* R,
+                                             int64_t rstride, int64_t rrow0, unsigned vblock,
+                                             unsigned char* smem_raw) {
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kYCells][kYCols]
   T* sf = su + NV * kYCells * kYCols;       // [NV][kYIfc][kYCols]
   T dt = T(0);
@@ -266,23 +298,25 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
     if (A.dt->zero) return;
     dt = (sizeof(T) == 4) ? T(A.dt->dt32) : T(A.dt->dt);
   }
-  const int64_t c0 = (int64_t)blockIdx.x * kYCols;
-  const int64_t r0 = (int64_t)blockIdx.y * kYTile;
+  const int64_t c0 = bx * kYCols;
+  const int64_t r0 = by * kYTile;
   const int ntile = (int)min((int64_t)kYTile, A.ny - r0);
   const int ncol = (int)min((int64_t)kYCols, A.nx - c0);
-  const int tx = threadIdx.x;
+  // kYCols x kYRowsT threads, in a (kYCols, kYRowsT) block or a flat one of the same size
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tx = tid % kYCols, ty = tid / kYCols;
   // stage rows r0-5 .. r0+ntile+4 (ntile + 10 <= kYCells) of the block's columns: one
   // row index per thread row and pass, all variables of it
   if (tx < ncol) {
     if (!A.f.active) {
-      for (int s = threadIdx.y; s < ntile + 10; s += kYRowsT) {
+      for (int s = ty; s < ntile + 10; s += kYRowsT) {
         const int64_t gr = ghost(r0 - 5 + s, A.ny, A.bc);
 #pragma unroll
         for (int v = 0; v < NV; ++v) su[(v * kYCells + s) * kYCols + tx] = A.u[v * A.fstride + gr * A.pitch + c0 + tx];
       }
     } else {
       const double tf = sweep_time(A);
-      for (int s = threadIdx.y; s < ntile + 10; s += kYRowsT)
+      for (int s = ty; s < ntile + 10; s += kYRowsT)
         for (int v = 0; v < NV; ++v)
           su[(v * kYCells + s) * kYCols + tx] =
               face_cell<T>(A.u, A.pitch, A.fstride, 1, c0 + tx, r0 - 5 + s, A.ny, A.bc, v, A.f, tf);
@@ -293,7 +327,7 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
   constexpr int p1 = (NV == 4) ? 2 : 1;
   constexpr int p2 = (NV == 4) ? 1 : 2;
   for (int q = 0; q < kYPer; ++q) {
-    const int t = threadIdx.y + kYRowsT * q;
+    const int t = ty + kYRowsT * q;
     bool fb = false;
     if (tx < ncol && t < ntile + 5) {
       T S[6][NV];
@@ -326,17 +360,17 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
   T rv[kYPer][NV];
 #pragma unroll
   for (int q = 0; q < kYPer; ++q) {
-    const int t = threadIdx.y + kYRowsT * q;
+    const int t = ty + kYRowsT * q;
     const bool on = tx < ncol && t < ntile;
-    const int64_t off = (r0 + t) * A.pitch + c0 + tx;
+    const T* rb = R + (r0 + t - rrow0) * A.pitch + c0 + tx;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) rv[q][k] = on ? A.R[k * A.fstride + off] : T(0);
+    for (int k = 0; k < NV; ++k) rv[q][k] = on ? __ldcg(rb + k * rstride) : T(0);
   }
   T wmx = T(0), wmy = T(0);
   bool wbad = false;
 #pragma unroll
   for (int q = 0; q < kYPer; ++q) {
-    const int t = threadIdx.y + kYRowsT * q;
+    const int t = ty + kYRowsT * q;
     if (tx < ncol && t < ntile) {
       const int64_t off = (r0 + t) * A.pitch + c0 + tx;
       T val[NV];
@@ -346,7 +380,8 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
         T Ly = flux_difference_family<T>(WCNS_OPT(FIX, A.s, family), f[0], f[kYCols], f[2 * kYCols], f[3 * kYCols], f[4 * kYCols],
                                   f[5 * kYCols], A.inv_h);
         // RHS: R = L_x.  Stage: R = a*un + b*(u + dt*L_x) from the x sweep.
-        val[k] = (MODE == kWriteL) ? rv[q][k] + Ly : rv[q][k] + ((A.general ? A.e : A.b) * dt) * Ly;
+        val[k] = (MODE == kWriteL) ? sadd<T>(rv[q][k], Ly)
+                                   : sfma<T>(smul<T>(A.general ? A.e : A.b, dt), Ly, rv[q][k]);
         A.out[k * A.fstride + off] = val[k];
       }
       if constexpr (MODE == kStage && NV == 4) {
@@ -363,8 +398,15 @@ __global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep
     }
   }
   if constexpr (MODE == kStage && NV == 4) {
-    if (A.wave) warp_wave<T>(wmx, wmy, wbad, A.wave, A.err);  // the same for every thread of the launch
+    if (A.wave) warp_wave<T>(wmx, wmy, wbad, vblock, A.wave, A.err);  // the same for every thread of the launch
   }
+}
+
+template <typename T, int NV, int MODE, int FIX>
+__global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep_y_kernel(SweepArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  sweep_y_body<T, NV, MODE, FIX>(A, blockIdx.x, blockIdx.y, A.R, A.fstride, 0, blockIdx.y * gridDim.x + blockIdx.x,
+                                 smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 #include "wcns_kernels.cuh"
 #include "wcns_adjoint_kernels.cuh"
 #include "wcns_stats.cuh"
+#include "wcns_band.cuh"
 
 namespace wcns {
 
@@ -221,6 +222,9 @@ cudaError_t configure_adjoints(int nvar) {
 }
 
 template <typename T>
+cudaError_t configure_band();
+
+template <typename T>
 cudaError_t configure_kernels(int nvar) {
   cudaError_t e;
   int dev = 0, nsm = 0;
@@ -231,6 +235,7 @@ cudaError_t configure_kernels(int nvar) {
   if (nvar > 1) (void)dt_wave_blocks<T>(nvar);  // occupancy query before any stream capture
   if ((e = configure_sweep_x<T>(nvar)) != cudaSuccess) return e;
   if ((e = configure_sweep_y<T>(nvar)) != cudaSuccess) return e;
+  if (nvar == 4 && (e = configure_band<T>()) != cudaSuccess) return e;
   return configure_adjoints<T>(nvar);
 }
 
@@ -298,6 +303,84 @@ cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T
     }
   }
   return cudaErrorInvalidValue;
+}
+
+// Resident blocks of one banded-stage kernel on the whole GPU (occupancy x SMs), read
+// at configuration time (before any stream capture).
+template <typename T, int FIX, int P>
+static int& band_blocks_nv() {
+  static int n = 0;
+  return n;
+}
+
+template <typename T, int FIX, int P>
+static cudaError_t configure_band_one() {
+  cudaError_t e = cudaFuncSetAttribute(stage_band_kernel<T, FIX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)stage_band_smem<T, P>());
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage_band_kernel<T, FIX, P>, kXThreads,
+                                                    stage_band_smem<T, P>());
+  if (e != cudaSuccess) return e;
+  band_blocks_nv<T, FIX, P>() = (occ > 0 ? occ : 1) * (sweep_sm_count() > 0 ? sweep_sm_count() : 1);
+  return cudaSuccess;
+}
+
+// x tiles per thread of the banded stage: four in single precision, one in double.
+template <typename T>
+constexpr int band_p() { return sizeof(T) == 4 ? 4 : 1; }
+
+// The banded stage is compiled for the default scheme configuration only (the FIX = 1
+// kernels), which keeps its build unit small.
+template <typename T>
+cudaError_t configure_band() {
+  return configure_band_one<T, 1, band_p<T>()>();
+}
+
+// The banded stage applies to 2D Euler stages of the default scheme configuration on
+// grids with enough bands to fill the ring; single precision also needs the grid to take
+// the wide (four-interface) x tiles.
+template <typename T>
+bool band_applies(const GridInfo& g, const Scheme& s) {
+  if (g.ndim != 2 || g.nvar != 4 || !use_fixed<4>(s)) return false;
+  if (sizeof(T) == 4 && !sweep_x_wide(g)) return false;
+  // work items are counted in int
+  const int64_t xt = (g.nx + sweep_x_tile<band_p<T>()>() - 1) / sweep_x_tile<band_p<T>()>();
+  const int64_t items = g.ny * xt + ((g.nx + kYCols - 1) / kYCols) * ((g.ny + kYTile - 1) / kYTile);
+  if (items >= ((int64_t)1 << 31)) return false;
+  return (g.ny + band_rows(g.ny) - 1) / band_rows(g.ny) > kBandRing;
+}
+
+// One 2D stage (x then y sweep of the same stage arguments as launch_sweep_x/_y) as a
+// banded persistent launch.  ring: band_ring_bytes(g, sizeof(T)); ctr: kBandCounters
+// zeroed words (left zeroed by the launch).
+template <typename T>
+cudaError_t launch_stage_band(const GridInfo& g, const Scheme& s, const SweepCall<T>& x, const SweepCall<T>& y,
+                              T* ring, unsigned* ctr, int* err, cudaStream_t st) {
+  constexpr int P = band_p<T>();
+  BandArgs<T> B{};
+  B.X = make_args<T>(g, s, 0, x);
+  B.Y = make_args<T>(g, s, 1, y);
+  B.plan = make_band_plan(g, sweep_x_tile<P>());
+  B.ring = ring;
+  B.ctr = ctr;
+  B.err = err;
+  if (!band_applies<T>(g, s)) return cudaErrorInvalidValue;
+  const int nitems = B.plan.seg_start[B.plan.nseg];
+  const int resident = band_blocks_nv<T, 1, P>();
+  if (resident <= 0) return cudaErrorInitializationError;
+  // a cooperative launch: every block is resident at once (the kernel's progress needs it)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)std::min(nitems, resident));
+  cfg.blockDim = dim3(kXThreads);
+  cfg.dynamicSmemBytes = stage_band_smem<T, P>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stage_band_kernel<T, 1, P>, B);
 }
 
 template <typename T>
@@ -419,6 +502,7 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
                                                cudaStream_t);                                        \
   extern template cudaError_t configure_sweep_y<T>(int);                                             \
   extern template cudaError_t configure_adjoints<T>(int);                                            \
+  extern template cudaError_t configure_band<T>();                                                   \
   }
 
 #define WCNS_INSTANTIATE_X(T, NV)                                                                    \
@@ -433,6 +517,14 @@ cudaError_t launch_weight_hist(const GridInfo& g, const Scheme& s, const Faces<d
   template cudaError_t configure_sweep_y<T>(int);                                                    \
   template cudaError_t launch_sweep_y<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,       \
                                          cudaStream_t);                                              \
+  }
+
+#define WCNS_INSTANTIATE_BAND(T)                                                                     \
+  namespace wcns {                                                                                   \
+  template cudaError_t configure_band<T>();                                                          \
+  template bool band_applies<T>(const GridInfo&, const Scheme&);                                     \
+  template cudaError_t launch_stage_band<T>(const GridInfo&, const Scheme&, const SweepCall<T>&,    \
+                                            const SweepCall<T>&, T*, unsigned*, int*, cudaStream_t); \
   }
 
 #define WCNS_INSTANTIATE_ADJ(T)                                                                      \

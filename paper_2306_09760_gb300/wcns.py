@@ -88,6 +88,7 @@ def load():
         "wcns_adjoint_step": (st, [vp, vp, ctypes.c_double, vp, vp]),
         "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
         "wcns_set_faces": (st, [vp, vp]),
+        "wcns_set_stage_form": (st, [vp, ctypes.c_int32]),
         "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
         "wcns_reciprocal_f64": (st, [vp, vp, ctypes.c_int64, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
@@ -231,6 +232,10 @@ def wcns_sync_status(ctx):
     n = ctypes.c_int64()
     s = load().wcns_sync_status(ctx, ctypes.byref(n))
     return s, n.value
+
+
+def wcns_set_stage_form(ctx, banded: bool):
+    _check(load().wcns_set_stage_form(ctx, int(bool(banded))), "wcns_set_stage_form")
 
 
 def wcns_profile_enable(ctx, on: bool):

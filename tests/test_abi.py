@@ -107,18 +107,19 @@ def test_batch_init_rejects_bad_layout_without_gpu(lib):
 
 def test_every_unit_is_built_and_every_family_instantiated():
     """Each .cu file under csrc is a build unit, and each kernel family (x sweeps per
-    variable count, y sweeps, adjoints, the rest) is instantiated exactly once per
+    variable count, y sweeps, adjoints, the banded 2D stage, the rest) is instantiated exactly once per
     element type, so no launcher is left undefined or defined twice at link time."""
     csrc = os.path.join(ROOT, "paper_2306_09760_gb300", "csrc")
     units = sorted(f for f in os.listdir(csrc) if f.endswith(".cu"))
     assert units == sorted(wbuild.UNITS)
     seen = {}
     for f in units:
-        for m in re.finditer(r"^WCNS_INSTANTIATE_(X|Y|ADJ|MISC)\((float|double)(?:, (\d))?\)", open(os.path.join(csrc, f)).read(), re.M):
+        for m in re.finditer(r"^WCNS_INSTANTIATE_(X|Y|ADJ|BAND|MISC)\((float|double)(?:, (\d))?\)", open(os.path.join(csrc, f)).read(), re.M):
             key = (m.group(1), m.group(2), m.group(3))
             assert key not in seen, (key, f, seen.get(key))
             seen[key] = f
     for t in ("float", "double"):
-        for fam in (("X", t, "1"), ("X", t, "3"), ("X", t, "4"), ("Y", t, None), ("ADJ", t, None), ("MISC", t, None)):
+        for fam in (("X", t, "1"), ("X", t, "3"), ("X", t, "4"), ("Y", t, None), ("ADJ", t, None), ("BAND", t, None),
+                    ("MISC", t, None)):
             assert fam in seen, fam
-    assert len(seen) == 12
+    assert len(seen) == 14
