@@ -56,7 +56,7 @@ constexpr int adj_x_min_blocks() { return sizeof(T) == 4 ? 6 : 1; }
 
 template <typename T, int NV, int MODE>
 __global__ void __launch_bounds__(kAXThreads, adj_x_min_blocks<T>()) adjoint_x_kernel(AdjArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);   // [NV][kXCells]
   T* sm = su + NV * kXCells;                // [NV][kXCells] mu
   T* sc = sm + NV * kXCells;                // [NV][6][kXThreads] per-interface stencil cotangents
@@ -147,7 +147,7 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(kAYCols * kAYRowsT, adj_y_min_blocks<T>()) adjoint_y_kernel(AdjArgs<T> A) {
   constexpr int kYCols = kAYCols, kYRowsT = kAYRowsT, kYPer = kAYPer, kYIfc = kAYIfc, kYTile = kAYTile,
                 kYCells = kAYCells;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);     // [NV][kYCells][kYCols]
   T* sm = su + NV * kYCells * kYCols;         // [NV][kYCells][kYCols]
   T* sc = sm + NV * kYCells * kYCols;         // [NV][6][kYIfc][kYCols]

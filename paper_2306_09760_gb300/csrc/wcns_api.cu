@@ -171,6 +171,7 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   x.faces = &c->faces;
   x.cstage = k.cstage;
   x.tnow = c->d_t;
+  x.status = c->d_err;
   if (c->g.ndim == 1) {
     x.un = static_cast<const T*>(un);
     x.out = static_cast<T*>(out);
@@ -202,6 +203,7 @@ cudaError_t sweeps(wcns_ctx* c, const void* u, const void* un, void* out, bool s
   y.faces = &c->faces;
   y.cstage = k.cstage;
   y.tnow = c->d_t;
+  y.status = c->d_err;
   if (stage_mode && k.last && c->fuse_wave) {
     y.wave = c->d_wave;
     y.err = c->d_err;

@@ -148,7 +148,7 @@ __device__ __forceinline__ void band_prepare(const BandArgs<T>& B, int item, int
 // and waits for what it depends on while the block is at a barrier.
 template <typename T, int FIX, int P>
 __global__ void __launch_bounds__(kXThreads, sweep_min_blocks<T>()) stage_band_kernel(const __grid_constant__ BandArgs<T> B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_job[5];
   const BandPlan& L = B.plan;
   if (B.X.dt && B.X.dt->zero) return;  // the run has reached t_end: every block leaves untouched

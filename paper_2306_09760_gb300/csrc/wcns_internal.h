@@ -47,6 +47,7 @@ struct SweepCall {
   // flagged in *err (else null)
   unsigned long long* wave;
   int* err;
+  int* status;  // sticky error word for bounded waits (always set)
 };
 template <typename T>
 cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st);

@@ -14,6 +14,8 @@
 // cells are produced by index arithmetic while the tile is staged in shared memory.
 #pragma once
 
+#include <cuda.h>
+
 #include "wcns_device.cuh"
 #include "wcns_pair.cuh"
 
@@ -50,7 +52,58 @@ struct SweepArgs {
   double cstage;                   // stage time t0 + cstage * dt of the state read (faces)
   const double* tnow;              // device time (faces, RHS without a step)
   int row_major;                   // x sweep: blockIdx.x = row, blockIdx.y = tile (else swapped)
+  // y sweep: tensor map of u as a (x, y, variable) tensor with a kYCols x kYCells x nvar
+  // box, used to stage the tiles whose rows all lie inside the grid (ytma = 1); else the
+  // per-thread loads stage every tile
+  int ytma;
+  int* status;                     // sticky error word (bit 1: a bounded wait ran out)
+  CUtensorMap ymap;
 };
+
+// ---------------------------------------------------------------------------
+// Tensor-memory-access (TMA) staging: one thread issues a bulk tensor copy of a whole
+// tile into shared memory, completed on an mbarrier that every thread of the block waits
+// on (bounded).
+// ---------------------------------------------------------------------------
+constexpr int kTmaSpin = 1 << 20;  // polls of the mbarrier before a wait gives up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(smem_u32(bar)), "r"(count) : "memory");
+  // make the initialised barrier visible to the async proxy (the copy engine)
+  asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" : : : "memory");
+}
+
+// Arms the barrier for `bytes` of transfer and issues the copy of the box at (x, y, z)
+// of the tensor map into dst.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x,
+                                            int y, int z, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];"
+      :
+      : "r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Waits until phase `parity` of the barrier has completed; false after kTmaSpin polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < kTmaSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 // Time of the state a sweep reads, for time-dependent boundary faces.
 template <typename T>
@@ -259,7 +312,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs<T>& A, int64_t row,
 
 template <typename T, int NV, int MODE, int FIX, int P, int TH = kXThreads>
 __global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(SweepArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int64_t row = A.row_major ? blockIdx.x : blockIdx.y;
   const int64_t tile = A.row_major ? blockIdx.y : blockIdx.x;
   sweep_x_body<T, NV, MODE, FIX, P, TH>(A, row, tile, A.out, A.fstride, 0, smem_raw);
@@ -306,8 +359,21 @@ __device__ __forceinline__ void sweep_y_body(const SweepArgs<T>& A, int64_t bx, 
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % kYCols, ty = tid / kYCols;
   // stage rows r0-5 .. r0+ntile+4 (ntile + 10 <= kYCells) of the block's columns: one
-  // row index per thread row and pass, all variables of it
-  if (tx < ncol) {
+  // bulk tensor copy of the kYCols x kYCells x NV box when every one of its rows lies in
+  // the grid (columns beyond nx arrive as zeros and are not used), else one row index per
+  // thread row and pass, all variables of it
+  const bool tma = A.ytma && !A.f.active && r0 - 5 >= 0 && r0 - 5 + kYCells <= A.ny;
+  __shared__ unsigned long long ybar;
+  if (tma) {
+    if (tid == 0) mbar_init(&ybar, 1);
+    __syncthreads();
+    if (tid == 0)
+      tma_load_3d(su, &A.ymap, &ybar, (int)c0, (int)(r0 - 5), 0, (unsigned)(sizeof(T) * NV * kYCells * kYCols));
+    if (!mbar_wait(&ybar, 0)) {
+      if (A.status) atomicOr(A.status, 2);
+      (void)mbar_wait(&ybar, 0);  // the copy may still land: wait (bounded) once more before the tile is used
+    }
+  } else if (tx < ncol) {
     if (!A.f.active) {
       for (int s = ty; s < ntile + 10; s += kYRowsT) {
         const int64_t gr = ghost(r0 - 5 + s, A.ny, A.bc);
@@ -323,6 +389,7 @@ __device__ __forceinline__ void sweep_y_body(const SweepArgs<T>& A, int64_t bx, 
     }
   }
   __syncthreads();
+  if (tma && tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" : : "r"(smem_u32(&ybar)) : "memory");
   // the sweep's normal ordering swaps the two momentum components
   constexpr int p1 = (NV == 4) ? 2 : 1;
   constexpr int p2 = (NV == 4) ? 1 : 2;
@@ -403,8 +470,9 @@ __device__ __forceinline__ void sweep_y_body(const SweepArgs<T>& A, int64_t bx, 
 }
 
 template <typename T, int NV, int MODE, int FIX>
-__global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>()) sweep_y_kernel(SweepArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kYCols * kYRowsT, sweep_min_blocks<T>())
+    sweep_y_kernel(const __grid_constant__ SweepArgs<T> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   sweep_y_body<T, NV, MODE, FIX>(A, blockIdx.x, blockIdx.y, A.R, A.fstride, 0, blockIdx.y * gridDim.x + blockIdx.x,
                                  smem_raw);
 }

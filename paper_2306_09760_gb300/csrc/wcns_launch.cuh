@@ -100,7 +100,35 @@ static SweepArgs<T> make_args(const GridInfo& g, const Scheme& s, int dir, const
   A.tnow = c.tnow;
   A.wave = c.wave;
   A.err = c.err;
+  A.status = c.status;
   return A;
+}
+
+// The tensor map of state buffer u as a (x, y, variable) tensor with the y sweep's
+// kYCols x kYCells x nvar box (columns beyond nx read as zeros); false when the driver
+// entry point is missing or refuses the layout (the sweep then stages with loads).  The
+// entry point is fetched through the runtime, so the library needs no link to libcuda.
+template <typename T>
+static bool encode_y_map(const GridInfo& g, const T* u, CUtensorMap* map) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static const EncodeFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeFn) nullptr;
+    return reinterpret_cast<EncodeFn>(f);
+  }();
+  if (!fn || !u || (reinterpret_cast<uintptr_t>(u) & 15u)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nvar};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * sizeof(T), (cuuint64_t)g.ny * (cuuint64_t)g.pitch * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)kYCols, (cuuint32_t)kYCells, (cuuint32_t)g.nvar};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+            const_cast<T*>(u), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T, int NV, int FIX, int P, int TH = kXThreads>
@@ -295,6 +323,7 @@ cudaError_t launch_sweep_x(const GridInfo& g, const Scheme& s, const SweepCall<T
 template <typename T>
 cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T>& c, cudaStream_t st) {
   SweepArgs<T> A = make_args<T>(g, s, 1, c);
+  A.ytma = encode_y_map<T>(g, A.u, &A.ymap) ? 1 : 0;
   switch (g.nvar) {
     case 1: return c.stage ? run_sweep_y<T, 1, kStage>(g, A, false, st) : run_sweep_y<T, 1, kWriteL>(g, A, false, st);
     case 4: {
@@ -361,6 +390,7 @@ cudaError_t launch_stage_band(const GridInfo& g, const Scheme& s, const SweepCal
   BandArgs<T> B{};
   B.X = make_args<T>(g, s, 0, x);
   B.Y = make_args<T>(g, s, 1, y);
+  B.Y.ytma = encode_y_map<T>(g, B.Y.u, &B.Y.ymap) ? 1 : 0;
   B.plan = make_band_plan(g, sweep_x_tile<P>());
   B.ring = ring;
   B.ctr = ctr;
