@@ -365,6 +365,9 @@ __device__ __forceinline__ void sweep_y_body(const SweepArgs<T>& A, int64_t bx, 
   const bool tma = A.ytma && !A.f.active && r0 - 5 >= 0 && r0 - 5 + kYCells <= A.ny;
   __shared__ unsigned long long ybar;
   if (tma) {
+    // every thread's earlier accesses of this shared memory (a previous tile of the block)
+    // precede the copy's writes (generic before async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" : : : "memory");
     if (tid == 0) mbar_init(&ybar, 1);
     __syncthreads();
     if (tid == 0)
