@@ -463,18 +463,32 @@ WCNS_HD T fe_null_distance(T w0, T w1, T w2, const SchemeT<T>& s) {
 
 // The saturated map (every tanh term +-1): the identity below the first and above the
 // last null point, the control values of Table 1 (Table B.1) in between.
+// a < b for weights and null points (non-negative): in double precision their bit
+// patterns, read as signed 64-bit integers, order like the values, so the compare runs
+// on the integer pipe instead of the FP64 pipe; in single precision the plain compare.
+template <typename T>
+WCNS_HD bool lt_nonneg(T a, T b) { return a < b; }
+template <>
+WCNS_HD bool lt_nonneg<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(a) < __double_as_longlong(b);
+#else
+  return a < b;
+#endif
+}
+
 template <typename T, int FAM>
 WCNS_HD void fe_staircase(T& w0, T& w1, T& w2, const SchemeT<T>& s) {
   const T c00 = FAM == 0 ? T(1.0 / 16.0) : s.ctrl0[0], c01 = FAM == 0 ? T(1.0 / 6.0) : s.ctrl0[1];
   const T c10 = FAM == 0 ? T(10.0 / 16.0) : s.ctrl1[0], c11 = FAM == 0 ? T(0.5) : s.ctrl1[1];
   const T c12 = FAM == 0 ? T(5.0 / 6.0) : s.ctrl1[2];
   const T c20 = FAM == 0 ? T(5.0 / 16.0) : s.ctrl2[0], c21 = FAM == 0 ? T(0.5) : s.ctrl2[1];
-  const T g0 = (w0 < fe_null<T, FAM>(s, 0, 1)) ? c00 : c01;
-  w0 = (w0 < fe_null<T, FAM>(s, 0, 0) || w0 > fe_null<T, FAM>(s, 0, 2)) ? w0 : g0;
-  const T g1 = (w1 < fe_null<T, FAM>(s, 1, 1)) ? c10 : ((w1 < fe_null<T, FAM>(s, 1, 2)) ? c11 : c12);
-  w1 = (w1 < fe_null<T, FAM>(s, 1, 0) || w1 > fe_null<T, FAM>(s, 1, 3)) ? w1 : g1;
-  const T g2 = (w2 < fe_null<T, FAM>(s, 2, 1)) ? c20 : c21;
-  w2 = (w2 < fe_null<T, FAM>(s, 2, 0) || w2 > fe_null<T, FAM>(s, 2, 2)) ? w2 : g2;
+  const T g0 = lt_nonneg<T>(w0, fe_null<T, FAM>(s, 0, 1)) ? c00 : c01;
+  w0 = (lt_nonneg<T>(w0, fe_null<T, FAM>(s, 0, 0)) || lt_nonneg<T>(fe_null<T, FAM>(s, 0, 2), w0)) ? w0 : g0;
+  const T g1 = lt_nonneg<T>(w1, fe_null<T, FAM>(s, 1, 1)) ? c10 : (lt_nonneg<T>(w1, fe_null<T, FAM>(s, 1, 2)) ? c11 : c12);
+  w1 = (lt_nonneg<T>(w1, fe_null<T, FAM>(s, 1, 0)) || lt_nonneg<T>(fe_null<T, FAM>(s, 1, 3), w1)) ? w1 : g1;
+  const T g2 = lt_nonneg<T>(w2, fe_null<T, FAM>(s, 2, 1)) ? c20 : c21;
+  w2 = (lt_nonneg<T>(w2, fe_null<T, FAM>(s, 2, 0)) || lt_nonneg<T>(fe_null<T, FAM>(s, 2, 2), w2)) ? w2 : g2;
 }
 
 // Eq. 20 for the three weights together.  Where every tanh argument of all three maps

@@ -170,7 +170,12 @@ def test_x_block_width_choice(W, kind, system, bc):
     check64(L, Lr, lambda u0: oracle.rhs(P, u0)[0], P.u0, f"{system} n={n} bc={bc}", strict=True)
     L32 = gpu_rhs(W, P, "f32")
     assert np.all(np.isfinite(L32))
-    assert np.abs(L32 - Lr).mean() / np.abs(Lr).mean() < 1e-4, np.abs(L32 - Lr).mean() / np.abs(Lr).mean()
+    err = np.abs(L32 - Lr)
+    print(f"\n{system} n={n} bc={bc} FP32 RHS: max / max|L| {err.max() / np.abs(Lr).max():.2e}")
+    assert err.mean() / np.abs(Lr).mean() < 1e-4, err.mean() / np.abs(Lr).mean()
+    # measured at most 5.9e-5 (1D Euler, 37901 cells); a misplaced ghost or tile-edge cell
+    # would put an error of the order of max|L| there
+    assert err.max() < 1e-3 * np.abs(Lr).max(), (err.max() / np.abs(Lr).max(), err.argmax())
 
 
 def test_fp64_device_reciprocal_against_ieee(W):

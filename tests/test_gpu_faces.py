@@ -57,7 +57,13 @@ def test_dmr_rhs_parity(W, family, time):
     Lr, _ = oracle.rhs(P, family=family, time=time)
     check64(L, Lr, lambda u0: oracle.rhs(P, u0, family=family, time=time)[0], P.u0, f"dmr {family} t={time}", strict=True)
     L32 = gpu_rhs(W, P, "f32", time=time, family=family)
-    assert np.abs(L32 - Lr).mean() / np.abs(Lr).mean() < 1e-4
+    err = np.abs(L32 - Lr)
+    print(f"\nDMR {family} t={time} FP32 RHS: relative L1 {err.mean() / np.abs(Lr).mean():.2e}, "
+          f"max / max|L| {err.max() / np.abs(Lr).max():.2e}")
+    assert err.mean() / np.abs(Lr).mean() < 1e-4
+    # measured 1.3e-7; a misplaced ghost or face cell would put an error of the order of
+    # max|L| there
+    assert err.max() < 1e-5 * np.abs(Lr).max(), (err.max() / np.abs(Lr).max(), np.unravel_index(err.argmax(), err.shape))
 
 
 def test_dmr_steps_parity_f64(W):
