@@ -463,9 +463,10 @@ WCNS_HD T fe_null_distance(T w0, T w1, T w2, const SchemeT<T>& s) {
 
 // The saturated map (every tanh term +-1): the identity below the first and above the
 // last null point, the control values of Table 1 (Table B.1) in between.
-// a < b for weights and null points (non-negative): in double precision their bit
-// patterns, read as signed 64-bit integers, order like the values, so the compare runs
-// on the integer pipe instead of the FP64 pipe; in single precision the plain compare.
+// a < b for a non-negative a (a weight, a ratio, a distance) and any non-NaN b: in double
+// precision the bit patterns, read as signed 64-bit integers, order like the values there,
+// so the compare runs on the integer pipe instead of the FP64 pipe; in single precision
+// the plain compare.
 template <typename T>
 WCNS_HD bool lt_nonneg(T a, T b) { return a < b; }
 template <>
@@ -592,15 +593,19 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
     }
     if (zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
     T a0 = T(0), a1 = T(0), a2 = T(0);
-    const bool small = weights == 2 && !wz && r0 < s.ideal_ratio && r1 < s.ideal_ratio && r2 < s.ideal_ratio;
+    // the ratios and |w_k - d_k| are non-negative, so these tests compare bit patterns
+    // in double precision (lt_nonneg)
+    const bool small = weights == 2 && !wz && lt_nonneg<T>(r0, s.ideal_ratio) && lt_nonneg<T>(r1, s.ideal_ratio) &&
+                       lt_nonneg<T>(r2, s.ideal_ratio);
     if (!small) {
       a0 = d0 * (T(1) + r0); a1 = d1 * (T(1) + r1); a2 = d2 * (T(1) + r2);
       const T isa = Num<T>::rcp_(a0 + a1 + a2);
       w0 = a0 * isa; w1 = a1 * isa; w2 = a2 * isa;
       if (wz) { wz[0] = w0; wz[1] = w1; wz[2] = w2; }
     }
-    if (small || (weights == 2 && s.ideal_margin[0] > T(0) && Num<T>::abs_(w0 - d0) < s.ideal_margin[0] &&
-                  Num<T>::abs_(w1 - d1) < s.ideal_margin[1] && Num<T>::abs_(w2 - d2) < s.ideal_margin[2])) {
+    if (small || (weights == 2 && s.ideal_margin[0] > T(0) && lt_nonneg<T>(Num<T>::abs_(w0 - d0), s.ideal_margin[0]) &&
+                  lt_nonneg<T>(Num<T>::abs_(w1 - d1), s.ideal_margin[1]) &&
+                  lt_nonneg<T>(Num<T>::abs_(w2 - d2), s.ideal_margin[2]))) {
       // inside the ideal plateaus (tested on the ratios, or on the weights): Eq. 20 and the
       // renormalisation give the ideal weights
       w0 = d0; w1 = d1; w2 = d2;
