@@ -43,7 +43,7 @@ constexpr int kBandMax = 64;                // bands per grid at most
 constexpr int kBandLead = 2;                // y tiles of band b follow the x tiles of band b + kBandLead
 constexpr int kBandRing = kBandLead + 2;    // partial-stage slots (at least kBandLead + 1)
 constexpr int kBandSpin = 1 << 22;          // polls (about 0.1 us each) before a wait gives up
-constexpr int kBandCounters = 2 + 2 * kBandMax;  // (unused), blocks done, x and y items done per band
+constexpr int kBandCounters = 2 + 2 * kBandMax;  // word 0 unused, blocks done, x and y items done per band
 
 // The work list of one banded stage (host-built, passed by value).
 struct BandPlan {
