@@ -212,6 +212,17 @@ wcns_status wcns_weight_hist(wcns_ctx* ctx, const void* u, int32_t nbins, uint64
  * advection.  Captured step graphs are dropped (rebuilt on the next wcns_step). */
 wcns_status wcns_set_faces(wcns_ctx* ctx, const wcns_faces* faces);
 
+/* Self-test of the library's bounded device waits (no counterpart in the paper: it checks
+ * the failure path of the kernels' waits without a GPU fault).  One thread waits, as the
+ * banded stage does, on a completion counter that nothing increments, then, as the
+ * TMA-staged tiles do, on an mbarrier armed for 16 bytes that no copy delivers.  Both
+ * waits must give up (each after about a second at most): gave_up[0] (counter) and
+ * gave_up[1] (mbarrier), a host array of 2, receive 1 when they did.  Each sets the
+ * sticky error bit, so the next wcns_sync_status returns WCNS_ERR_TIMEOUT (and clears
+ * it); the context stays usable.  Synchronises the context stream.
+ * Errors: WCNS_ERR_ARG (null pointer), WCNS_ERR_CUDA. */
+wcns_status wcns_selftest_waits(wcns_ctx* ctx, int32_t* gave_up);
+
 /* Chooses how the RK stages of a 2D Euler grid run (steps (a)-(e) and the stage update
  * of wcns_step; the scheme itself, Eq. 2-3 with the TVD-RK3 or Eq. 16 stages, is the
  * same either way, and so is every result, bit for bit).

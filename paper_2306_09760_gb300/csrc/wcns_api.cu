@@ -685,6 +685,20 @@ wcns_status wcns_set_faces(wcns_ctx* c, const wcns_faces* f) {
   return WCNS_OK;
 }
 
+wcns_status wcns_selftest_waits(wcns_ctx* c, int32_t* gave_up) {
+  if (!c || !gave_up) return WCNS_ERR_ARG;
+  // word 0 of the banded-stage counters is zeroed at init and never written: a counter
+  // that nothing increments; the results go to the context's scalar outputs
+  int* d_res = reinterpret_cast<int*>(c->d_out);
+  WCNS_TRY(launch_wait_selftest(c->d_band, c->d_err, d_res, c->stream));
+  int h[2] = {0, 0};
+  WCNS_TRY(cudaMemcpyAsync(h, d_res, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  WCNS_TRY(cudaStreamSynchronize(c->stream));
+  gave_up[0] = h[0];
+  gave_up[1] = h[1];
+  return WCNS_OK;
+}
+
 wcns_status wcns_set_stage_form(wcns_ctx* c, int32_t banded) {
   if (!c) return WCNS_ERR_ARG;
   if (banded) {

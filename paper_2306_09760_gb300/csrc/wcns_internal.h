@@ -64,6 +64,10 @@ template <typename T>
 cudaError_t launch_stage_band(const GridInfo& g, const Scheme& s, const SweepCall<T>& x, const SweepCall<T>& y,
                               T* ring, unsigned* ctr, int* err, cudaStream_t st);
 size_t band_ring_bytes_of(const GridInfo& g, size_t elem);
+// One-thread kernel whose two bounded waits (a completion counter that nothing
+// increments, an mbarrier that no copy fills) must both give up: gave_up[0..1] (device)
+// receive 1 when they did; each sets bit 1 of *err.  `never` must stay 0.
+cudaError_t launch_wait_selftest(const unsigned* never, int* err, int* gave_up, cudaStream_t st);
 constexpr int kBandCounterWords = 2 + 2 * 64;
 
 // Adjoint sweep: out = c1*X1 + c2*X2 + b*(mu + dt*(R + J^T mu)) (combine) or

@@ -65,7 +65,8 @@ struct SweepArgs {
 // tile into shared memory, completed on an mbarrier that every thread of the block waits
 // on (bounded).
 // ---------------------------------------------------------------------------
-constexpr int kTmaSpin = 1 << 20;  // polls of the mbarrier before a wait gives up
+constexpr int kTmaSpin = 1 << 20;         // polls of the mbarrier before a wait gives up
+constexpr unsigned kTmaPollNs = 1000;     // suspend-time hint of one poll (ns): a wait lasts about a second at most
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -91,14 +92,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Waits until phase `parity` of the barrier has completed; false after kTmaSpin polls.
+// Waits until phase `parity` of the barrier has completed; false after kTmaSpin polls,
+// each suspended for at most about kTmaPollNs.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
   for (int it = 0; it < kTmaSpin; ++it) {
     unsigned done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kTmaPollNs)
         : "memory");
     if (done) return true;
   }

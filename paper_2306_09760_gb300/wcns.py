@@ -89,6 +89,7 @@ def load():
         "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
         "wcns_set_faces": (st, [vp, vp]),
         "wcns_set_stage_form": (st, [vp, ctypes.c_int32]),
+        "wcns_selftest_waits": (st, [vp, P(ctypes.c_int32)]),
         "wcns_reduce_noalloc": (st, [P(wcns_grid), vp, vp, ctypes.c_int32, vp, vp]),
         "wcns_reciprocal_f64": (st, [vp, vp, ctypes.c_int64, vp]),
         "wcns_sync_status": (st, [vp, P(ctypes.c_int64)]),
@@ -232,6 +233,13 @@ def wcns_sync_status(ctx):
     n = ctypes.c_int64()
     s = load().wcns_sync_status(ctx, ctypes.byref(n))
     return s, n.value
+
+
+def wcns_selftest_waits(ctx):
+    """[counter wait gave up, mbarrier wait gave up] (both should be 1)."""
+    out = (ctypes.c_int32 * 2)()
+    _check(load().wcns_selftest_waits(ctx, out), "wcns_selftest_waits")
+    return [int(out[0]), int(out[1])]
 
 
 def wcns_set_stage_form(ctx, banded: bool):
