@@ -676,11 +676,11 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
     rstar_np = inputs.vortex_primitive(n, t=T)[0]
     res = {"cells": n * n, "steps": steps, "dt": dt, "alpha": amax,
            "config": "isentropic vortex (strength 5, mean flow (1, 1)) on periodic [0,10]^2, 512^2, 1% density "
-                     "noise (seed 0), 200 TVD-RK3 steps of constant dt (CFL 0.5 at t = 0), LLF with alpha frozen "
+                     "noise (seed 0), 200 TVD-RK3 steps of constant dt (CFL 0.5 at t = 0), RK-stage checkpoints, LLF with alpha frozen "
                      "at the initial maximum wave speed, FE xi = 100, Z p = 2, characteristic, eps = 1e-4 (raised "
                      "from 1e-40 so the 200-step tangent stays bounded), J = 1/2 h^2 sum (rho(T) - rho*)^2"}
 
-    def make_J(S, tdt):
+    def make_J(S, tdt, stages=True):
         U = torch.as_tensor(P.extra["u"], device="cuda", dtype=tdt)
         V = torch.as_tensor(P.extra["v"], device="cuda", dtype=tdt)
         pr = torch.as_tensor(P.extra["p"], device="cuda", dtype=tdt)
@@ -688,7 +688,7 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
 
         def J(rho0):
             E = pr / 0.4 + 0.5 * rho0 * (U * U + V * V)
-            uT = wag.rollout(torch.stack([rho0, rho0 * U, rho0 * V, E]), S, dt, steps)
+            uT = wag.rollout(torch.stack([rho0, rho0 * U, rho0 * V, E]), S, dt, steps, stages=stages)
             return 0.5 * h * h * torch.sum((uT[0] - rstar) ** 2)
         return J
 
@@ -711,6 +711,19 @@ def run_adjoint_variant(W, torch, inputs, steps=200):
         res[prec] = {"J": float(Jv.detach()), "forward_s": t1 - t0, "adjoint_s": t2 - t1,
                      "forward_mcells": n * n * steps / (t1 - t0) / 1e6,
                      "adjoint_mcells": n * n * steps / (t2 - t1) / 1e6}
+        if prec == "f32":
+            # the same gradient with per-step state checkpoints only (the adjoint step
+            # recomputes the two inner RK stages)
+            Jr = make_J(S, tdt, stages=False)
+            torch.cuda.synchronize()
+            Jrv = Jr(rho0)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            (gr,) = torch.autograd.grad(Jrv, rho0)
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+            res[prec]["adjoint_mcells_recompute"] = n * n * steps / (t4 - t3) / 1e6
+            res[prec]["recompute_gradient_identical"] = bool(torch.equal(gr, g))
         if prec == "f64":
             dirn = torch.as_tensor(np.random.default_rng(3).normal(size=(n, n)), device="cuda")
             ad = float(torch.sum(g * dirn))

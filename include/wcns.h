@@ -291,6 +291,26 @@ wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void
 wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const void* lam_np1,
                               void* lam_n);
 
+/* wcns_adjoint_step with the step's two inner TVD-RK3 stage states supplied by the caller
+ * (RK-stage checkpoints, e.g. written by wcns_step_stages during the forward pass)
+ * instead of recomputed from u_n: the reverse sweeps run at u2, u1 and u_n exactly as
+ * in wcns_adjoint_step, so both give the same lam_n bit for bit when u1, u2 are the
+ * step's stages.  u_n, u1, u2: device grid buffers of the step, 16-byte aligned, not
+ * aliasing lam_np1 or lam_n.  Same options, errors and allocation as wcns_adjoint_step.
+ * Asynchronous. */
+wcns_status wcns_adjoint_step_stages(wcns_ctx* ctx, const void* u_n, const void* u1, const void* u2, double dt,
+                                     const void* lam_np1, void* lam_n);
+
+/* One TVD-RK3 step of fixed size dt > 0 on u in place, as wcns_step(ctx, u, dt, 1, 0),
+ * that also writes its two inner stage states, u1 = u + dt L(u) and
+ * u2 = 3/4 u + 1/4 (u1 + dt L(u1)), into the caller's u1_out and u2_out (device grid
+ * buffers, 16-byte aligned, distinct from u and from each other) instead of the
+ * context's stage scratch: the forward half of RK-stage checkpointing for
+ * wcns_adjoint_step_stages.  The device time advances by dt.  Errors: WCNS_ERR_ARG
+ * (pointers, aliasing, dt <= 0), WCNS_ERR_UNSUPPORTED (integrator WCNS_RK4).
+ * Asynchronous. */
+wcns_status wcns_step_stages(wcns_ctx* ctx, void* u, double dt, void* u1_out, void* u2_out);
+
 /* The device reciprocal behind every double-precision division of the sweeps and the CFL
  * step computation: out[i] = 1 / x[i] by two steps of Newton's iteration for the
  * reciprocal from the reciprocal unit's approximation.  No counterpart in the paper: it

@@ -321,7 +321,11 @@ cudaError_t adjoint_stage(wcns_ctx* c, const void* u, const void* mu, const void
 // the step comes from the CFL maxima the previous step's last stage reduced, instead of
 // a CFL kernel reading u^n.  On 2D Euler grids every step's last stage reduces them.
 cudaError_t rk_step_io(wcns_ctx* c, const void* src, void* u, void* out, double dt, double t_end,
-                       bool from_maxima = false) {
+                       bool from_maxima = false, void* s1 = nullptr, void* s2 = nullptr) {
+  // s1, s2: where the TVD-RK3 step writes its two inner stage states (default: the
+  // context's stage scratch)
+  void* u1 = s1 ? s1 : c->u1;
+  void* u2 = s2 ? s2 : c->u2;
   cudaError_t e;
   if (from_maxima && c->fuse_wave && src == u) {
     if ((e = dt_from_maxima(c, dt, t_end)) != cudaSuccess) return e;
@@ -339,9 +343,9 @@ cudaError_t rk_step_io(wcns_ctx* c, const void* src, void* u, void* out, double 
     return stage_coef(c, c->u3, u, out, k4);
   }
   // stage times t, t + dt, t + dt/2
-  if ((e = stage(c, u, nullptr, c->u1, 0.0, 1.0, 0.0)) != cudaSuccess) return e;
-  if ((e = stage(c, c->u1, u, c->u2, 0.75, 0.25, 1.0)) != cudaSuccess) return e;
-  return stage(c, c->u2, u, out, 1.0 / 3.0, 2.0 / 3.0, 0.5, true);
+  if ((e = stage(c, u, nullptr, u1, 0.0, 1.0, 0.0)) != cudaSuccess) return e;
+  if ((e = stage(c, u1, u, u2, 0.75, 0.25, 1.0)) != cudaSuccess) return e;
+  return stage(c, u2, u, out, 1.0 / 3.0, 2.0 / 3.0, 0.5, true);
 }
 
 cudaError_t rk3_step(wcns_ctx* c, void* u, double dt, double t_end, bool from_maxima) {
@@ -433,6 +437,39 @@ __global__ void reciprocal_f64_kernel(const double* x, double* out, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = Num<double>::rcp_(x[i]);
 }
+}  // namespace
+
+namespace {
+// Options the hand-written adjoint covers.
+bool adjoint_supported(const wcns_ctx* c) {
+  const wcns_params& p = c->p;
+  return p.system == WCNS_EULER && p.flux == WCNS_FLUX_LLF_FROZEN && p.weights != WCNS_W_M &&
+         p.integrator == WCNS_RK3 && p.family == WCNS_FAMILY_WCNS && !c->faces.active;
+}
+
+// The three reverse RK stages of one TVD-RK3 step, at the step's stage states u_n, u1, u2.
+wcns_status adjoint_from_stages(wcns_ctx* c, const void* u_n, const void* u1, const void* u2, double dt,
+                                     const void* lam_np1, void* lam_n) {
+  const size_t bytes = c->nelem * c->elem;
+  if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
+  if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
+  // reverse of u' = 1/3 u + 2/3 (u2 + dt L(u2)), u2 = 3/4 u + 1/4 (u1 + dt L(u1)), u1 = u + dt L(u):
+  //   a2 = 2/3 (lam + dt J(u2)^T lam)
+  //   a1 = 1/4 (a2 + dt J(u1)^T a2)
+  //   lam_n = 1/3 lam + 3/4 a2 + (a1 + dt J(u)^T a1)
+  auto reverse_stage = [&](const void* u, const void* mu, const void* X1, double c1, const void* X2, double c2,
+                           double b, void* out) -> cudaError_t {
+    return by_type(
+        c->g.dtype,
+        [&] { return adjoint_stage<double>(c, u, mu, X1, c1, X2, c2, b, dt, out); },
+        [&] { return adjoint_stage<float>(c, u, mu, X1, c1, X2, c2, b, dt, out); });
+  };
+  WCNS_TRY(reverse_stage(u2, lam_np1, nullptr, 0.0, nullptr, 0.0, 2.0 / 3.0, c->adj1));
+  WCNS_TRY(reverse_stage(u1, c->adj1, nullptr, 0.0, nullptr, 0.0, 0.25, c->adj2));
+  WCNS_TRY(reverse_stage(u_n, c->adj2, lam_np1, 1.0 / 3.0, c->adj1, 0.75, 1.0, lam_n));
+  return WCNS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -715,33 +752,33 @@ wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const voi
   if (!c || !u_n || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(lam_np1) || !aligned16(lam_n))
     return WCNS_ERR_ARG;
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
-  const wcns_params& p = c->p;
-  if (p.system != WCNS_EULER || p.flux != WCNS_FLUX_LLF_FROZEN || p.weights == WCNS_W_M ||
-      p.integrator != WCNS_RK3 || p.family != WCNS_FAMILY_WCNS || c->faces.active)
-    return WCNS_ERR_UNSUPPORTED;
-  const size_t bytes = c->nelem * c->elem;
-  if (!c->adj1) WCNS_TRY(cudaMalloc(&c->adj1, bytes));
-  if (!c->adj2) WCNS_TRY(cudaMalloc(&c->adj2, bytes));
+  if (!adjoint_supported(c)) return WCNS_ERR_UNSUPPORTED;
   // stage states of the forward step, recomputed from the checkpoint u_n
   const StepDt step{dt, 0.0, (float)dt, 0};
   WCNS_TRY(cudaMemcpyAsync(c->d_dt, &step, sizeof(step), cudaMemcpyHostToDevice, c->stream));
   WCNS_TRY(stage(c, u_n, nullptr, c->u1, 0.0, 1.0, 0.0));
   WCNS_TRY(stage(c, c->u1, u_n, c->u2, 0.75, 0.25, 1.0));
-  // reverse of u' = 1/3 u + 2/3 (u2 + dt L(u2)), u2 = 3/4 u + 1/4 (u1 + dt L(u1)), u1 = u + dt L(u):
-  //   a2 = 2/3 (lam + dt J(u2)^T lam)
-  //   a1 = 1/4 (a2 + dt J(u1)^T a2)
-  //   lam_n = 1/3 lam + 3/4 a2 + (a1 + dt J(u)^T a1)
-  auto reverse_stage = [&](const void* u, const void* mu, const void* X1, double c1, const void* X2, double c2,
-                           double b, void* out) -> cudaError_t {
-    return by_type(
-        c->g.dtype,
-        [&] { return adjoint_stage<double>(c, u, mu, X1, c1, X2, c2, b, dt, out); },
-        [&] { return adjoint_stage<float>(c, u, mu, X1, c1, X2, c2, b, dt, out); });
-  };
-  WCNS_TRY(reverse_stage(c->u2, lam_np1, nullptr, 0.0, nullptr, 0.0, 2.0 / 3.0, c->adj1));
-  WCNS_TRY(reverse_stage(c->u1, c->adj1, nullptr, 0.0, nullptr, 0.0, 0.25, c->adj2));
-  WCNS_TRY(reverse_stage(u_n, c->adj2, lam_np1, 1.0 / 3.0, c->adj1, 0.75, 1.0, lam_n));
-  return WCNS_OK;
+  return adjoint_from_stages(c, u_n, c->u1, c->u2, dt, lam_np1, lam_n);
+}
+
+wcns_status wcns_adjoint_step_stages(wcns_ctx* c, const void* u_n, const void* u1, const void* u2, double dt,
+                                     const void* lam_np1, void* lam_n) {
+  if (!c || !u_n || !u1 || !u2 || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(u1) || !aligned16(u2) ||
+      !aligned16(lam_np1) || !aligned16(lam_n))
+    return WCNS_ERR_ARG;
+  if (!(dt > 0.0)) return WCNS_ERR_ARG;
+  if (!adjoint_supported(c)) return WCNS_ERR_UNSUPPORTED;
+  return adjoint_from_stages(c, u_n, u1, u2, dt, lam_np1, lam_n);
+}
+
+wcns_status wcns_step_stages(wcns_ctx* c, void* u, double dt, void* u1_out, void* u2_out) {
+  if (!c || !u || !u1_out || !u2_out || !aligned16(u) || !aligned16(u1_out) || !aligned16(u2_out)) return WCNS_ERR_ARG;
+  if (u1_out == u || u2_out == u || u1_out == u2_out) return WCNS_ERR_ARG;
+  if (!(dt > 0.0)) return WCNS_ERR_ARG;
+  if (c->p.integrator != WCNS_RK3) return WCNS_ERR_UNSUPPORTED;
+  // the first step of a call: the CFL kernel writes the step record (fixed dt) and
+  // advances the device time, as wcns_step(ctx, u, dt, 1, 0) does
+  return from_cuda(rk_step_io(c, u, u, u, dt, 0.0, false, u1_out, u2_out));
 }
 
 wcns_status wcns_reciprocal_f64(const double* x, double* out, int64_t n, void* stream) {

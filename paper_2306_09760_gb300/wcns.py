@@ -86,6 +86,8 @@ def load():
         "wcns_get_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_int64)]),
         "wcns_reduce": (st, [vp, vp, vp, ctypes.c_int32, P(ctypes.c_double)]),
         "wcns_adjoint_step": (st, [vp, vp, ctypes.c_double, vp, vp]),
+        "wcns_adjoint_step_stages": (st, [vp, vp, vp, vp, ctypes.c_double, vp, vp]),
+        "wcns_step_stages": (st, [vp, vp, ctypes.c_double, vp, vp]),
         "wcns_weight_hist": (st, [vp, vp, ctypes.c_int32, vp]),
         "wcns_set_faces": (st, [vp, vp]),
         "wcns_set_stage_form": (st, [vp, ctypes.c_int32]),
@@ -226,6 +228,15 @@ def wcns_set_faces(ctx, faces=None):
 
 def wcns_adjoint_step(ctx, u_n, dt: float, lam_np1, lam_n):
     _check(load().wcns_adjoint_step(ctx, _ptr(u_n), float(dt), _ptr(lam_np1), _ptr(lam_n)), "wcns_adjoint_step")
+
+
+def wcns_adjoint_step_stages(ctx, u_n, u1, u2, dt: float, lam_np1, lam_n):
+    _check(load().wcns_adjoint_step_stages(ctx, _ptr(u_n), _ptr(u1), _ptr(u2), float(dt), _ptr(lam_np1),
+                                           _ptr(lam_n)), "wcns_adjoint_step_stages")
+
+
+def wcns_step_stages(ctx, u, dt: float, u1_out, u2_out):
+    _check(load().wcns_step_stages(ctx, _ptr(u), float(dt), _ptr(u1_out), _ptr(u2_out)), "wcns_step_stages")
 
 
 def wcns_sync_status(ctx):

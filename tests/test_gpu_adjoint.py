@@ -368,3 +368,51 @@ def test_fp32_gradient_of_the_adjoint_workload(W):
           f"(bound {bound:.2e})")
     assert grad_err < bound, (grad_err, fwd_level)
     assert min(fd_errs) < bound, (fd_errs, fwd_level)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rk_stage_checkpoints_equal_recomputation(W, dtype):
+    """RK-stage checkpointing: wcns_step_stages advances the state exactly as wcns_step
+    does and hands out the two inner stage states; wcns_adjoint_step_stages on them gives
+    the lam_n of wcns_adjoint_step (which recomputes them) bit for bit, and the autograd
+    rollout gives the same gradient with either kind of checkpoint.  On the adjoint
+    workload's setup at 128^2, 6 steps, transmissive-free (periodic) vortex data."""
+    import torch
+    from paper_2306_09760_gb300 import autograd as wag
+    P, dt, params = _c5_setup(128)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = W.Solver(P, dtype, stream=stream, **params)
+        ua = S.u.clone()
+        ub = S.u.clone()
+        ck = []
+        for _ in range(6):
+            un = ub.clone()
+            u1, u2 = S.alloc(), S.alloc()
+            W.wcns_step(S.ctx, ua, dt, 1, 0.0)
+            W.wcns_step_stages(S.ctx, ub, dt, u1, u2)
+            ck.append((un, u1, u2))
+        stream.synchronize()
+        assert torch.equal(ua, ub)
+        rng = np.random.default_rng(5)
+        lam_a = S.set_state(rng.normal(size=P.u0.shape), S.alloc())
+        lam_b = lam_a.clone()
+        for un, u1, u2 in reversed(ck):
+            W.wcns_adjoint_step(S.ctx, un, dt, lam_a, lam_a)
+            W.wcns_adjoint_step_stages(S.ctx, un, u1, u2, dt, lam_b, lam_b)
+        stream.synchronize()
+        assert torch.equal(lam_a, lam_b)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        grads = []
+        for stages in (True, False):
+            u0 = torch.as_tensor(P.u0, device="cuda", dtype=tdt).clone().requires_grad_(True)
+            uT = wag.rollout(u0, S, dt, 4, stages=stages)
+            (g,) = torch.autograd.grad((uT[0] ** 2).sum(), u0)
+            grads.append(g)
+        assert torch.equal(grads[0], grads[1])
+        st, _ = S.status()
+        with pytest.raises(W.WcnsError) as e:
+            W.wcns_step_stages(S.ctx, S.u, dt, S.u, u2)  # a stage buffer aliasing u
+        assert e.value.status == W.WCNS_ERR_ARG
+        S.close()
+    assert st == W.WCNS_OK
