@@ -582,21 +582,33 @@ WCNS_HD T weno_side(T v0, T v1, T v2, T v3, T v4, const SchemeT<T>& s, T* wz = n
   } else {
     // Eq. 14-15
     T tau = Num<T>::abs_(is0 - is2);
-    T r0, r1, r2;
+    T r0 = T(0), r1 = T(0), r2 = T(0);
     const T b0 = is0 + eps, b1 = is1 + eps, b2 = is2 + eps;
-    if constexpr (sizeof(T) == 8) {
-      // one division for the three ratios (the product of three IS + eps stays in range)
-      const T q = Num<T>::div_(tau, b0 * b1 * b2);
-      r0 = q * (b1 * b2); r1 = q * (b0 * b2); r2 = q * (b0 * b1);
-    } else {
-      r0 = Num<T>::z_ratio(tau, b0); r1 = Num<T>::z_ratio(tau, b1); r2 = Num<T>::z_ratio(tau, b2);
+    // the ratios, tau and |w_k - d_k| are non-negative, so the plateau tests compare bit
+    // patterns in double precision (lt_nonneg)
+    bool small = false;
+    if (weights == 2 && !wz && zp == 1) {
+      // r_k = tau / b_k < ideal_ratio  <=>  tau < ideal_ratio b_k (b_k > 0), tested before
+      // the ratios are formed, against a bound lowered by 1e-6; just below the bound the
+      // tests that follow reach the same weights
+      const T qv = s.ideal_ratio * T(0.999999);
+      small = lt_nonneg<T>(tau, qv * b0) && lt_nonneg<T>(tau, qv * b1) && lt_nonneg<T>(tau, qv * b2);
     }
-    if (zp == 2) { r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2; }
+    if (!small) {
+      if constexpr (sizeof(T) == 8) {
+        // one division for the three ratios (the product of three IS + eps stays in range)
+        const T q = Num<T>::div_(tau, b0 * b1 * b2);
+        r0 = q * (b1 * b2); r1 = q * (b0 * b2); r2 = q * (b0 * b1);
+      } else {
+        r0 = Num<T>::z_ratio(tau, b0); r1 = Num<T>::z_ratio(tau, b1); r2 = Num<T>::z_ratio(tau, b2);
+      }
+      if (zp == 2) {
+        r0 = r0 * r0; r1 = r1 * r1; r2 = r2 * r2;
+        small = weights == 2 && !wz && lt_nonneg<T>(r0, s.ideal_ratio) && lt_nonneg<T>(r1, s.ideal_ratio) &&
+                lt_nonneg<T>(r2, s.ideal_ratio);
+      }
+    }
     T a0 = T(0), a1 = T(0), a2 = T(0);
-    // the ratios and |w_k - d_k| are non-negative, so these tests compare bit patterns
-    // in double precision (lt_nonneg)
-    const bool small = weights == 2 && !wz && lt_nonneg<T>(r0, s.ideal_ratio) && lt_nonneg<T>(r1, s.ideal_ratio) &&
-                       lt_nonneg<T>(r2, s.ideal_ratio);
     if (!small) {
       a0 = d0 * (T(1) + r0); a1 = d1 * (T(1) + r1); a2 = d2 * (T(1) + r2);
       const T isa = Num<T>::rcp_(a0 + a1 + a2);

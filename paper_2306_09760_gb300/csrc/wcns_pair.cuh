@@ -119,12 +119,25 @@ __device__ __forceinline__ P2 weno_pair(P2 v0, P2 v1, P2 v2, P2 v3, P2 v4, const
     // Eq. 14-15 with the single-precision cap of the ratio
     const P2 tau = abs(sub(is0, is2));
     float t0, t1;
+    if (weights == 2 && zp == 1 && (Fixed<FIX>::on || s.ideal_ratio > 0.0f)) {
+      // r_k = tau / b_k < ideal_ratio  <=>  tau < ideal_ratio b_k (b_k > 0), tested before
+      // the ratios are formed, against a bound lowered by 1e-6: where it holds, both lanes'
+      // Z weights lie inside the ideal plateaus of Eq. 20 (see SchemeT::ideal_ratio) and
+      // Eq. 6 takes the ideal weights; just below the bound the tests that follow reach
+      // the same weights
+      const P2 qv = bc(s.ideal_ratio * 0.999999f);
+      float c0l, c0r, c1l, c1r, c2l, c2r;
+      split(mul(qv, b0), c0l, c0r); split(mul(qv, b1), c1l, c1r); split(mul(qv, b2), c2l, c2r);
+      split(tau, t0, t1);
+      if (t0 < c0l && t1 < c0r && t0 < c1l && t1 < c1r && t0 < c2l && t1 < c2r)
+        return fma(bc(d2), q2, fma(bc(d1), q1, mul(bc(d0), q0)));
+    }
     P2 r0 = mul(tau, rcp(b0)), r1 = mul(tau, rcp(b1)), r2 = mul(tau, rcp(b2));
     split(r0, t0, t1); r0 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     split(r1, t0, t1); r1 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     split(r2, t0, t1); r2 = mk(fminf(t0, 1.0e18f), fminf(t1, 1.0e18f));
     if (zp == 2) { r0 = mul(r0, r0); r1 = mul(r1, r1); r2 = mul(r2, r2); }
-    if (weights == 2 && (Fixed<FIX>::on || s.ideal_ratio > 0.0f)) {
+    if (weights == 2 && zp == 2 && s.ideal_ratio > 0.0f) {
       // every ratio of both lanes below ideal_ratio: the Z weights lie inside the ideal
       // plateaus of Eq. 20 (see SchemeT::ideal_ratio), so the mapped and renormalised
       // weights are the ideal ones, without normalising the Z weights first
