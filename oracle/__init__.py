@@ -8,11 +8,13 @@ function follows.
 Parity status: every function is pinned by `tests/test_oracle_*.py` against values
 the paper prints (Table 1 and Table B.1 control values), closed forms (the linear scheme's Fourier
 symbol, polynomial exactness, Eq. 18 truncation coefficients, the exact Riemann
-solution, the JS and M weights of Eq. 11-13 in exact rational arithmetic, the CFL
+solution, the JS, M and Z weights of Eq. 11-15 in exact rational arithmetic, the CFL
 step of uniform states and of the Sod tube), invariants (conservation, symmetry) and
-central finite differences.
-The weight statistics (`weight_hist`) are parity unpinned: the paper's Tables A.1-A.4
-depend on solver settings it does not state.
+central finite differences.  The weight statistics (`weight_hist`) are pinned by a
+brute-force enumeration of one L(u)'s one-sided interpolations with the Z weights of
+Eq. 14-15 in exact fractions and the Table 1 staircase, and by the sample counts that
+Eq. 3 and App. B fix; the absolute shares of Tables A.1-A.4 are not reproduced, since
+they depend on solver settings the paper does not state.
 """
 from __future__ import annotations
 

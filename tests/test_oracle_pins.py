@@ -653,3 +653,138 @@ def test_cfl_step_clipped_at_t_end():
     t_end = 2.5 * dt0
     _, t, taken, _ = oracle.step(P, dt=0.0, nsteps=10, t_end=t_end, cfl=0.5)
     assert t == t_end and taken == 3
+
+
+# ---------------------------------------------------------------------------
+# App. A weight statistics: the histogram of every one-sided interpolation of one L(u)
+# ---------------------------------------------------------------------------
+IDEAL = (Fraction(1, 16), Fraction(10, 16), Fraction(5, 16))
+# Table 1 control values between consecutive null points (kappa = 1/2, xi = 1e6)
+PLATEAUS = {0: [Fraction(1, 16), Fraction(1, 6)],
+            1: [Fraction(10, 16), Fraction(1, 2), Fraction(5, 6)],
+            2: [Fraction(5, 16), Fraction(1, 2)]}
+NULLS_EXACT = {0: [Fraction(1, 32), (Fraction(1, 16) + Fraction(1, 11)) / 2, (Fraction(1, 11) + 1) / 2],
+               1: [Fraction(10, 32), (Fraction(10, 16) + Fraction(2, 3)) / 2,
+                   (Fraction(2, 3) + Fraction(10, 11)) / 2, (Fraction(10, 11) + 1) / 2],
+               2: [Fraction(5, 32), (Fraction(5, 16) + Fraction(1, 3)) / 2, (Fraction(1, 3) + 1) / 2]}
+
+
+def _z_weights_exact(v, eps, p=1):
+    """Eq. 14-15 in exact fractions: alpha_k = d_k (1 + (tau / (IS_k + eps))^p), tau = |IS_0 - IS_2|,
+    with IS_k = f_k^2 + s_k^2 (Eq. 9) from the derivatives of the sub-stencil quadratics (Eq. 10)."""
+    v = [Fraction(x) for x in v]
+    IS = []
+    for k in range(3):
+        f, s = _quadratic_derivatives_at_xi([k - 2, k - 1, k], v[k:k + 3])
+        IS.append(f * f + s * s)
+    tau = abs(IS[0] - IS[2])
+    alpha = [d * (1 + (tau / (b + eps)) ** p) for d, b in zip(IDEAL, IS)]
+    tot = sum(alpha)
+    return [a / tot for a in alpha]
+
+
+def _staircase_exact(k, w):
+    """Eq. 20 at xi = 1e6 away from its null points: the identity below the first and above
+    the last null point, the Table 1 control value between two of them."""
+    z = NULLS_EXACT[k]
+    j = sum(w > zz for zz in z)
+    return w if j in (0, len(z)) else PLATEAUS[k][j - 1]
+
+
+def _periodic_line(n):
+    """Dyadic values (exact in binary) on a periodic line: a quadratic, a jump of 3, a
+    linear ramp, a plateau, a cubic and a kink, so that smooth, one-jump and two-jump
+    stencils all occur."""
+    v = []
+    for j in range(n):
+        if j < 10:
+            x = Fraction(j, 8)
+            v.append(x * x)
+        elif j < 18:
+            v.append(3 + Fraction(j, 16))
+        elif j < 24:
+            v.append(Fraction(5, 2))
+        elif j < 32:
+            x = Fraction(j - 28, 4)
+            v.append(x * x * x / 8)
+        else:
+            v.append(Fraction(abs(j - 36), 2))
+    return v
+
+
+def test_weight_hist_brute_force_in_exact_fractions():
+    """App. A statistics, pinned by brute force: on a periodic scalar line, enumerate the
+    interfaces k+1/2 that Eq. 3 reads for one L(u) (k = -3..n+1, so F at i-5/2..i+5/2 exists
+    for every cell), form both one-sided 5-cell stencils (the right-biased one mirrored),
+    compute the Z weights of Eq. 14-15 in exact fractions and the final weights through the
+    Table 1 staircase and the renormalisation, bin each into [0, 1] / nbins, and compare
+    with the oracle's histograms bin for bin."""
+    n, nb = 40, 10000
+    vals = _periodic_line(n)
+    P = inputs.advection_sine(n)
+    P.u0[0, 0, :] = [float(x) for x in vals]
+    assert all(Fraction(float(x)) == x for x in vals)
+    eps = Fraction(1e-40)
+
+    def binned(w):
+        # floor(w nbins + 1e-6), clipped; the bin must not change within 1e-9 of the
+        # exact value, far more than the oracle's rounding of w moves w nbins
+        x = w * nb + Fraction(1, 10 ** 6)
+        lo, hi = (min(nb - 1, math.floor(x + d)) for d in (-Fraction(1, 10 ** 9), Fraction(1, 10 ** 9)))
+        assert lo == hi, "weight on a bin edge"
+        return lo
+
+    want = np.zeros((2, 3, nb), dtype=np.int64)
+    samples = 0
+    for k in range(-3, n + 2):
+        cells = [vals[(k - 2 + s) % n] for s in range(6)]
+        for stencil in (cells[0:5], cells[5:0:-1]):
+            wz = _z_weights_exact(stencil, eps)
+            for i in range(3):
+                assert min(abs(wz[i] - zz) for zz in NULLS_EXACT[i]) > Fraction(1, 10 ** 4)
+            g = [_staircase_exact(i, wz[i]) for i in range(3)]
+            wf = [x / sum(g) for x in g]
+            for i in range(3):
+                want[0, i, binned(wz[i])] += 1
+                want[1, i, binned(wf[i])] += 1
+            samples += 1
+    got, ns = oracle.weight_hist(P, nbins=nb)
+    assert ns == samples == 2 * (n + 5)
+    np.testing.assert_array_equal(got, want)
+    # the data reach every kind of stencil: ideal, intermediate and near-zero weights
+    assert want[1, 1, 6250] > 0 and want[1, 1, 5000] > 0 and want[0, 1, :100].sum() > 0
+
+
+@pytest.mark.parametrize("ndim,family,lines", [(1, "WCNS", (64,)), (2, "WCNS", (24, 16)),
+                                                (1, "WENO", (64,)), (2, "WENO", (24, 16))])
+def test_weight_hist_sample_counts(ndim, family, lines):
+    """Every one-sided interpolation of one L(u) is counted once: Eq. 3 reads n + 5
+    interfaces per line (F at i-5/2..i+5/2 for i = 0..n-1), the two-point difference of
+    App. B n + 1; each interface has two one-sided interpolations per characteristic field
+    (left and right states, or the f+ and f- halves of the split flux), and each histogram
+    row sums to the sample count."""
+    if ndim == 1:
+        P = inputs.sod(lines[0])
+        per = lambda m: m + (5 if family == "WCNS" else 1)
+        want = 2 * P.nvar * per(P.nx)
+    else:
+        P = inputs.riemann2d(lines[0], seed=0, ny=lines[1])
+        per = lambda m: m + (5 if family == "WCNS" else 1)
+        want = 2 * P.nvar * (P.ny * per(P.nx) + P.nx * per(P.ny))
+    h, ns = oracle.weight_hist(P, nbins=1000, family=family)
+    assert ns == want
+    assert np.all(h.sum(axis=2) == ns)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("case", range(len(JS_STENCILS)))
+def test_z_weights_eq14_15_exact(case, p):
+    """Eq. 14-15: the oracle's Z weights agree with the exact rational value on the Eq. 11
+    stencils (eps comparable with IS, so its place in Eq. 14 matters), for p = 1 and 2;
+    with the FE map off they are also the final weights."""
+    v, eps = JS_STENCILS[case]
+    want = _z_weights_exact(v, eps, p=p)
+    _, wz, wf, mapped = oracle.interp([float(x) for x in v], weights="Z", eps=float(eps), zp=p)
+    assert mapped == 0
+    np.testing.assert_allclose(wz, [float(w) for w in want], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(wz, wf)
