@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -119,14 +120,29 @@ class ClockSampler:
 SWEEP_SOURCES = ("wcns_device.cuh", "wcns_pair.cuh", "wcns_kernels.cuh", "wcns_band.cuh")
 
 
+_CODE_TOKENS = re.compile(rb'"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'|//[^\n]*|/\*.*?\*/|\s+', re.S)
+
+
+def code_only(src: bytes) -> bytes:
+    """C++ source with comments dropped and every run of white space made one blank
+    (string and character literals kept as written)."""
+    def sub(m):
+        t = m.group(0)
+        if t.startswith(b"//") or t.startswith(b"/*") or t[:1].isspace():
+            return b" "
+        return t
+    return re.sub(rb" +", b" ", _CODE_TOKENS.sub(sub, src)).strip()
+
+
 def kernel_source_digest(read=None):
-    """Digest of the sweep and CFL kernels' sources (read(name) -> bytes; default: the
-    working tree)."""
+    """Digest of the sweep and CFL kernels' code (read(name) -> bytes; default: the
+    working tree).  Comments and white space do not enter it, so the stored counters of a
+    capture stay valid across edits that change neither."""
     d = os.path.join(ROOT, "paper_2306_09760_gb300", "csrc")
     read = read or (lambda name: open(os.path.join(d, name), "rb").read())
     h = hashlib.sha256()
     for name in SWEEP_SOURCES:
-        h.update(name.encode() + read(name))
+        h.update(name.encode() + code_only(read(name)))
     return h.hexdigest()[:16]
 
 

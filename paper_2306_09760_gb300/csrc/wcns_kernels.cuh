@@ -3,11 +3,14 @@
 //
 // Sweep structure (per RK stage, Eq. 2-3 + steps (a)-(e)):
 //   1D:  sweep_x computes L and the stage update in one kernel.
-//   2D:  sweep_x writes L_x into a scratch plane set; sweep_y computes L_y, adds L_x
-//        and applies the stage update.  Splitting the sweeps keeps the redundant
-//        interface work at the tile edges to ~2% per sweep (a fused 2D tile of
-//        32 x 32 cells recomputes ~16% of its interfaces), and the extra plane
-//        traffic (one write + one read of L_x) is hidden under the arithmetic.
+//   2D:  sweep_x writes the partial stage a*u^n + b*(u + dt*L_x) (L_x alone for an RHS
+//        evaluation) into a scratch plane set; sweep_y computes L_y and completes the
+//        stage as R + b*dt*L_y.  Splitting the sweeps keeps the redundant interface
+//        work at the tile edges small (x: 5 interfaces per 251- or 1019-cell tile;
+//        y: 80 interfaces for 75 rows), where a fused 2D tile of 32 x 32 cells
+//        recomputes ~16% of its interfaces; the extra plane traffic (one write and one
+//        read of R) is hidden under the arithmetic.  The banded form (wcns_band.cuh)
+//        runs both sweeps of a stage in one persistent launch with R kept in L2.
 //
 // A tile of T output cells along a line needs the T + 5 interfaces
 // F_{c0-5/2} .. F_{c0+T-1+5/2}, which need the T + 10 cells c0-5 .. c0+T+4.  Ghost
@@ -321,8 +324,8 @@ __global__ void __launch_bounds__(TH, sweep_min_blocks<T>()) sweep_x_kernel(Swee
 }
 
 // ---------------------------------------------------------------------------
-// y sweep: one block per (32 columns, kYTile rows); 32 x 8 threads, each thread
-// computes kYPer interfaces of its column.  Stage: out = R + b*dt*L_y with R the
+// y sweep: one block per (kYCols columns, kYTile rows); kYCols x kYRowsT threads, each
+// computing kYPer interfaces of its column.  Stage: out = R + b*dt*L_y with R the
 // partial stage of the x sweep; RHS: out = R + L_y with R = L_x.
 // ---------------------------------------------------------------------------
 // 16 columns x 16 thread rows: a tall tile keeps the 5-row halo small (80 interfaces
