@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "wcns_internal.h"
 #include "wcns_kernels.cuh"
@@ -32,16 +33,22 @@ static cudaError_t run_sweep_x_per(const GridInfo& g, const SweepArgs<T>& A0, bo
   return cudaGetLastError();
 }
 
-// SM count of the current device, read by configure_kernels (before any launch or capture).
-inline int& sweep_sm_count() {
-  static int nsm = 0;
+// SM count of the current device, written by configure_kernels (before any launch or
+// capture).  Contexts may be created and used on several host threads, so the value and
+// the occupancy figures below are atomics.
+inline std::atomic<int>& sweep_sm_count() {
+  static std::atomic<int> nsm{0};
   return nsm;
+}
+inline int sm_count_or_one() {
+  const int n = sweep_sm_count().load(std::memory_order_relaxed);
+  return n > 0 ? n : 1;
 }
 
 // Four interfaces per thread (single-precision Euler systems) when the grid gives at
 // least two full waves of such blocks (four per SM), else one.
 inline bool sweep_x_wide(const GridInfo& g) {
-  const int nsm = sweep_sm_count() > 0 ? sweep_sm_count() : 1;
+  const int nsm = sm_count_or_one();
   const int64_t blocks = g.ny * ((g.nx + sweep_x_tile<4>() - 1) / sweep_x_tile<4>());
   return blocks >= 2 * 4 * (int64_t)nsm;
 }
@@ -50,7 +57,7 @@ inline bool sweep_x_wide(const GridInfo& g) {
 // 256-thread tiles would give fewer blocks than SMs: a line of 4096 cells then spreads
 // over 152 blocks of 27 cells instead of 17 blocks of 251, at 5/27 redundant interfaces.
 inline bool sweep_x_narrow(const GridInfo& g) {
-  const int nsm = sweep_sm_count() > 0 ? sweep_sm_count() : 1;
+  const int nsm = sm_count_or_one();
   const int64_t blocks = g.ny * ((g.nx + sweep_x_tile<1>() - 1) / sweep_x_tile<1>());
   return blocks < (int64_t)nsm;
 }
@@ -202,15 +209,17 @@ static cudaError_t configure_adjoint() {
 // Resident blocks of the CFL kernel on the whole GPU (occupancy x SMs), read once.
 template <typename T, int NV>
 static int64_t dt_wave_blocks_nv() {
-  static int64_t cached = 0;
-  if (cached <= 0) {
+  static std::atomic<int64_t> cached{0};
+  int64_t n = cached.load(std::memory_order_relaxed);
+  if (n <= 0) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dt_kernel<T, NV>, kRedThreads, 0) != cudaSuccess ||
         occ <= 0)
       occ = 1;
-    cached = (int64_t)occ * (sweep_sm_count() > 0 ? sweep_sm_count() : 1);
+    n = (int64_t)occ * sm_count_or_one();
+    cached.store(n, std::memory_order_relaxed);
   }
-  return cached;
+  return n;
 }
 template <typename T>
 static int64_t dt_wave_blocks(int nvar) {
@@ -258,7 +267,7 @@ cudaError_t configure_kernels(int nvar) {
   int dev = 0, nsm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  sweep_sm_count() = nsm;
+  sweep_sm_count().store(nsm, std::memory_order_relaxed);
   if (nvar != 1 && nvar != 3 && nvar != 4) return cudaErrorInvalidValue;
   if (nvar > 1) (void)dt_wave_blocks<T>(nvar);  // occupancy query before any stream capture
   if ((e = configure_sweep_x<T>(nvar)) != cudaSuccess) return e;
@@ -337,8 +346,8 @@ cudaError_t launch_sweep_y(const GridInfo& g, const Scheme& s, const SweepCall<T
 // Resident blocks of one banded-stage kernel on the whole GPU (occupancy x SMs), read
 // at configuration time (before any stream capture).
 template <typename T, int FIX, int P>
-static int& band_blocks_nv() {
-  static int n = 0;
+static std::atomic<int>& band_blocks_nv() {
+  static std::atomic<int> n{0};
   return n;
 }
 
@@ -351,7 +360,7 @@ static cudaError_t configure_band_one() {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, stage_band_kernel<T, FIX, P>, kXThreads,
                                                     stage_band_smem<T, P>());
   if (e != cudaSuccess) return e;
-  band_blocks_nv<T, FIX, P>() = (occ > 0 ? occ : 1) * (sweep_sm_count() > 0 ? sweep_sm_count() : 1);
+  band_blocks_nv<T, FIX, P>().store((occ > 0 ? occ : 1) * sm_count_or_one(), std::memory_order_relaxed);
   return cudaSuccess;
 }
 
@@ -397,7 +406,7 @@ cudaError_t launch_stage_band(const GridInfo& g, const Scheme& s, const SweepCal
   B.err = err;
   if (!band_applies<T>(g, s)) return cudaErrorInvalidValue;
   const int nitems = B.plan.seg_start[B.plan.nseg];
-  const int resident = band_blocks_nv<T, 1, P>();
+  const int resident = band_blocks_nv<T, 1, P>().load(std::memory_order_relaxed);
   if (resident <= 0) return cudaErrorInitializationError;
   // a cooperative launch: every block is resident at once (the kernel's progress needs it)
   cudaLaunchConfig_t cfg{};
