@@ -235,7 +235,7 @@ wcns_status wcns_selftest_waits(wcns_ctx* ctx, int32_t* gave_up);
  *     algorithmic DRAM bytes (read u and u^n once, write the stage once) instead of about
  *     twice that.  On GB300 the sweeps are bound by instruction issue, not by DRAM, and
  *     the persistent loop's per-tile synchronisation costs more than the traffic saves
- *     (2048^2: 0.32 ms against 0.24 ms per FP32 stage), hence not the default.  It
+ *     (2048^2: 0.30 ms against 0.22 ms per FP32 stage), hence not the default.  It
  *     applies to 2D Euler grids of the default scheme configuration (FE weights with
  *     the Table 2 rows at kappa = 0.5, xi >= 1e4, Z p = 1, renormalised, HLLC,
  *     characteristic) with more than four bands of rows (bands are whole 75-row y
