@@ -123,3 +123,101 @@ def test_every_unit_is_built_and_every_family_instantiated():
                     ("MISC", t, None)):
             assert fam in seen, fam
     assert len(seen) == 14
+
+
+def test_binding_structures_match_the_header_layout():
+    """The binding's ctypes descriptors (wcns_grid, wcns_params, wcns_faces) have the C
+    header's size and field offsets: a C program compiled against include/wcns.h prints
+    sizeof and offsetof of every field the binding declares."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2306_09760_gb300 import wcns
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [wcns.wcns_grid, wcns.wcns_params, wcns.wcns_faces]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "wcns.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, *_ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", exe, src],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=30).stdout
+    c_layout = {}
+    for line in out.split("\n"):
+        if line.strip():
+            a, b, v = line.split()
+            c_layout[(a, b)] = int(v)
+    for st in structs:
+        name = st.__name__
+        assert c_layout[(name, "size")] == ctypes.sizeof(st), name
+        for field, *_ in st._fields_:
+            assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
+
+
+def _header_prototypes():
+    """name -> (return type, [parameter types]) for every function declared in include/*.h."""
+    protos = {}
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, fn)).read(), flags=re.S)
+        for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**)\s*(wcns_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                             text, re.M):
+            params = []
+            for p in m.group(3).split(","):
+                p = " ".join(p.split())
+                if p in ("", "void"):
+                    continue
+                typ = re.sub(r"\s*\b[A-Za-z_][A-Za-z0-9_]*$", "", p)  # drop the parameter name
+                params.append(typ.replace(" *", "*"))
+            protos[m.group(2)] = (" ".join(m.group(1).split()).replace(" *", "*"), params)
+    return protos
+
+
+def test_binding_signatures_match_the_header_prototypes(lib):
+    """Every entry point's ctypes restype and argtypes agree with its C prototype: scalars
+    by exact type, pointers to scalars or descriptors by pointee (or as a void pointer),
+    opaque handles and buffers as void pointers, out-handles as pointers to them."""
+    L = lib.load()
+    scalars = {"double": ctypes.c_double, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+               "wcns_status": ctypes.c_int}
+    structs = {"wcns_grid": lib.wcns_grid, "wcns_params": lib.wcns_params, "wcns_faces": lib.wcns_faces}
+
+    def matches(ctype, ct):
+        base = ctype.replace("const ", "").strip()
+        if base in scalars:
+            return ct is scalars[base]
+        if base == "void":
+            return ct is None
+        if base == "char*":
+            return ct is ctypes.c_char_p
+        if base in ("void*", "wcns_ctx*", "wcns_batch*"):
+            return ct is ctypes.c_void_p
+        if base in ("wcns_ctx**", "wcns_batch**"):
+            return ct is ctypes.POINTER(ctypes.c_void_p)
+        if base.endswith("*") and base.count("*") == 1:
+            pointee = base[:-1]
+            want = scalars.get(pointee) or structs.get(pointee)
+            if pointee == "uint64_t":
+                want = ctypes.c_uint64
+            return want is not None and (ct is ctypes.c_void_p or ct is ctypes.POINTER(want))
+        return False
+
+    protos = _header_prototypes()
+    assert len(protos) == len(declared_functions())
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        assert matches(ret, f.restype), (name, ret, f.restype)
+        assert f.argtypes is not None and len(f.argtypes) == len(params), (name, params, f.argtypes)
+        for i, (p, ct) in enumerate(zip(params, f.argtypes)):
+            assert matches(p, ct), (name, i, p, ct)
