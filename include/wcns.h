@@ -285,7 +285,8 @@ wcns_status wcns_reduce_noalloc(const wcns_grid* grid, const void* a, const void
  * Supported: WCNS_EULER (ndim 1 or 2), WCNS_FLUX_LLF_FROZEN (a smooth flux), weights
  * JS / Z / FE / PFE, characteristic 0 or 1, WCNS_RK3, WCNS_FAMILY_WCNS; otherwise
  * WCNS_ERR_UNSUPPORTED.
- * lam_np1 and lam_n may be the same buffer; u_n must not alias either.  The first
+ * lam_np1 and lam_n may be the same buffer; u_n must not alias either (the same pointer
+ * returns WCNS_ERR_ARG; a partial overlap is not detected).  The first
  * call allocates two cotangent buffers of the context (nvar*ny*pitch each).
  * Asynchronous. */
 wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const void* lam_np1,
@@ -296,7 +297,8 @@ wcns_status wcns_adjoint_step(wcns_ctx* ctx, const void* u_n, double dt, const v
  * instead of recomputed from u_n: the reverse sweeps run at u2, u1 and u_n exactly as
  * in wcns_adjoint_step, so both give the same lam_n bit for bit when u1, u2 are the
  * step's stages.  u_n, u1, u2: device grid buffers of the step, 16-byte aligned, not
- * aliasing lam_np1 or lam_n.  Same options, errors and allocation as wcns_adjoint_step.
+ * aliasing lam_np1 or lam_n (the same pointer returns WCNS_ERR_ARG).  Same options,
+ * errors and allocation as wcns_adjoint_step.
  * Asynchronous. */
 wcns_status wcns_adjoint_step_stages(wcns_ctx* ctx, const void* u_n, const void* u1, const void* u2, double dt,
                                      const void* lam_np1, void* lam_n);

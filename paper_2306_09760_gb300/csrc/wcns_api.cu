@@ -751,6 +751,7 @@ wcns_status wcns_set_stage_form(wcns_ctx* c, int32_t banded) {
 wcns_status wcns_adjoint_step(wcns_ctx* c, const void* u_n, double dt, const void* lam_np1, void* lam_n) {
   if (!c || !u_n || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(lam_np1) || !aligned16(lam_n))
     return WCNS_ERR_ARG;
+  if (u_n == lam_np1 || u_n == lam_n) return WCNS_ERR_ARG;  // the checkpoint is read after lam_n is written
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
   if (!adjoint_supported(c)) return WCNS_ERR_UNSUPPORTED;
   // stage states of the forward step, recomputed from the checkpoint u_n
@@ -766,6 +767,8 @@ wcns_status wcns_adjoint_step_stages(wcns_ctx* c, const void* u_n, const void* u
   if (!c || !u_n || !u1 || !u2 || !lam_np1 || !lam_n || !aligned16(u_n) || !aligned16(u1) || !aligned16(u2) ||
       !aligned16(lam_np1) || !aligned16(lam_n))
     return WCNS_ERR_ARG;
+  for (const void* q : {u_n, u1, u2})
+    if (q == lam_np1 || q == lam_n) return WCNS_ERR_ARG;  // the stage states are read after lam_n is written
   if (!(dt > 0.0)) return WCNS_ERR_ARG;
   if (!adjoint_supported(c)) return WCNS_ERR_UNSUPPORTED;
   return adjoint_from_stages(c, u_n, u1, u2, dt, lam_np1, lam_n);

@@ -414,5 +414,12 @@ def test_rk_stage_checkpoints_equal_recomputation(W, dtype):
         with pytest.raises(W.WcnsError) as e:
             W.wcns_step_stages(S.ctx, S.u, dt, S.u, u2)  # a stage buffer aliasing u
         assert e.value.status == W.WCNS_ERR_ARG
+        un, u1, u2 = ck[-1]
+        with pytest.raises(W.WcnsError) as e:
+            W.wcns_adjoint_step(S.ctx, un, dt, lam_a, un)  # the cotangent written over the checkpoint
+        assert e.value.status == W.WCNS_ERR_ARG
+        with pytest.raises(W.WcnsError) as e:
+            W.wcns_adjoint_step_stages(S.ctx, un, u1, u2, dt, u1, lam_b)  # a stage state as the cotangent
+        assert e.value.status == W.WCNS_ERR_ARG
         S.close()
     assert st == W.WCNS_OK
