@@ -788,3 +788,24 @@ def test_z_weights_eq14_15_exact(case, p):
     assert mapped == 0
     np.testing.assert_allclose(wz, [float(w) for w in want], rtol=0, atol=1e-15)
     np.testing.assert_array_equal(wz, wf)
+
+
+@pytest.mark.parametrize("params", [dict(), dict(weights="JS", flux="ROE"), dict(weights="M", flux="LLF"),
+                                    dict(characteristic=False, zp=2), dict(family="WENO")])
+def test_periodic_shift_equivariance(params):
+    """On a periodic grid the scheme is translation invariant: L(shift(u)) = shift(L(u)) bit
+    for bit, for shifts across the wrap in both directions (the ghost cells of Eq. 3's
+    stencils come from the other end of the line, so a wrap-around index error breaks it)."""
+    P = inputs.rough_euler_2d(24, 20, seed=3)
+    L, _ = oracle.rhs(P, **params)
+    for sx, sy in ((1, 0), (0, 1), (5, -3), (-7, 11)):
+        Q = inputs.Problem("shifted", 2, 4, P.nx, P.ny, P.lo, P.hi, P.bc,
+                           np.roll(P.u0, (sy, sx), axis=(1, 2)).copy(), 1)
+        Ls, _ = oracle.rhs(Q, **params)
+        np.testing.assert_array_equal(Ls, np.roll(L, (sy, sx), axis=(1, 2)))
+    P1 = inputs.random_smooth_euler_1d(37, seed=2)
+    L1, _ = oracle.rhs(P1, **params)
+    for s in (1, -4, 18):
+        Q1 = inputs.Problem("shifted1d", 1, 3, P1.nx, 1, P1.lo, P1.hi, P1.bc,
+                            np.roll(P1.u0, s, axis=2).copy(), 1)
+        np.testing.assert_array_equal(oracle.rhs(Q1, **params)[0], np.roll(L1, s, axis=2))
