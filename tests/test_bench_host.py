@@ -49,11 +49,17 @@ def test_clock_summary_without_samples_says_unavailable(tmp_path):
     assert r["samples"] == 0 and r["sm_mhz"] is None and r["reasons"] == ["unavailable"]
 
 
-def test_measured_peaks_come_from_the_driver_file():
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        want = float(json.load(f)["hbm_gbs"])
+def test_measured_peaks_come_from_the_measured_file():
+    """The HBM peak is the measured copy bandwidth in MEASURED_PEAKS.json when that file is
+    present, else the stated fallback (6.8 TB/s, labelled as such)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     got, src = bench.measured_peaks()
-    assert src == "measured" and got == want
+    if os.path.exists(path):
+        with open(path) as f:
+            want = float(json.load(f)["hbm_gbs"])
+        assert src == "measured" and got == want
+    else:
+        assert src == "fallback" and got == 6800.0
 
 
 def test_roofline_takes_the_kernel_with_the_most_time():
