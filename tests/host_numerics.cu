@@ -1,0 +1,56 @@
+// Test tool: the library's double-precision interface numerics (wcns_device.cuh) compiled
+// for the host, behind a C interface the CPU tests load with ctypes.  On the host the
+// divisions are IEEE divisions and the comparisons plain ones (the device build uses
+// Newton reciprocals and bit-pattern compares), so results agree with the device up to
+// rounding; the tests compare them with the oracle interface by interface.
+#include "../paper_2306_09760_gb300/csrc/wcns_device.cuh"
+
+using namespace wcns;
+
+static SchemeT<double> make_scheme(int system, int weights, int flux, int characteristic, int zp, int family,
+                                   double xi, double eps, double alpha) {
+  Scheme s{};
+  s.system = system; s.weights = weights; s.flux = flux; s.characteristic = characteristic; s.zp = zp;
+  s.renorm = 1; s.gamma = 1.4; s.eps = eps; s.xi = xi; s.cv = 1e-3; s.harten = 0.1;
+  s.speed[0] = alpha; s.speed[1] = alpha;
+  fill_family_tables(s, family, 0.5);
+  return scheme_as<double>(s);
+}
+
+template <int NV, int FIX>
+static int flux_nv(const SchemeT<double>& st, const double* S, double* F) {
+  double SS[6][NV], FF[NV];
+  for (int m = 0; m < 6; ++m)
+    for (int k = 0; k < NV; ++k) SS[m][k] = S[m * NV + k];
+  const bool fb = interface_flux<double, NV, FIX>(SS, st, 0, FF);
+  for (int k = 0; k < NV; ++k) F[k] = FF[k];
+  return fb ? 1 : 0;
+}
+
+extern "C" {
+
+// Midpoint flux of the interface between cells 2 and 3 of S[6][nvar] (x normal, Euler),
+// with run-time options (fixed = 0) or the compiled default configuration (fixed = 1).
+// Returns 1 if the interface fell back to (U_i, U_{i+1}), -1 on an unsupported nvar.
+int host_interface_flux(int nvar, int weights, int flux, int characteristic, int zp, int family, double xi,
+                        double eps, double alpha, int fixed, const double* S, double* F) {
+  const SchemeT<double> st = make_scheme(1, weights, flux, characteristic, zp, family, xi, eps, alpha);
+  if (nvar == 3) return fixed ? flux_nv<3, 1>(st, S, F) : flux_nv<3, 0>(st, S, F);
+  if (nvar == 4) return fixed ? flux_nv<4, 1>(st, S, F) : flux_nv<4, 0>(st, S, F);
+  return -1;
+}
+
+// One-sided midpoint interpolation of v[0..4] (WCNS family): the value, and the base and
+// final weights in wz[3], wf[3].
+double host_weno_side(int weights, int zp, double xi, double eps, const double* v, double* wz, double* wf) {
+  const SchemeT<double> st = make_scheme(0, weights, 0, 0, zp, 0, xi, eps, 0.0);
+  return weno_side<double, 0>(v[0], v[1], v[2], v[3], v[4], st, wz, wf);
+}
+
+// Eq. 3 (WCNS family) or the two-point difference (WENO family) of six midpoint fluxes
+// f[0..5] = F_{i-5/2} .. F_{i+5/2}, divided by h = 1 / inv_h.
+double host_flux_difference(int family, const double* f, double inv_h) {
+  return flux_difference_family<double>(family, f[0], f[1], f[2], f[3], f[4], f[5], inv_h);
+}
+
+}  // extern "C"
