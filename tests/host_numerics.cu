@@ -1,9 +1,11 @@
-// Test tool: the library's double-precision interface numerics (wcns_device.cuh) compiled
+// Test tool: the library's double-precision interface numerics (wcns_device.cuh) and their
+// reverse sweep (wcns_adjoint.cuh) compiled
 // for the host, behind a C interface the CPU tests load with ctypes.  On the host the
 // divisions are IEEE divisions and the comparisons plain ones (the device build uses
 // Newton reciprocals and bit-pattern compares), so results agree with the device up to
 // rounding; the tests compare them with the oracle interface by interface.
 #include "../paper_2306_09760_gb300/csrc/wcns_device.cuh"
+#include "../paper_2306_09760_gb300/csrc/wcns_adjoint.cuh"
 
 using namespace wcns;
 
@@ -27,6 +29,17 @@ static int flux_nv(const SchemeT<double>& st, const double* S, double* F) {
   return fb ? 1 : 0;
 }
 
+template <int NV>
+static void vjp_nv(const SchemeT<double>& st, const double* S, const double* Fb, double* Sb) {
+  double SS[6][NV], FB[NV], SB[6][NV];
+  for (int m = 0; m < 6; ++m)
+    for (int k = 0; k < NV; ++k) { SS[m][k] = S[m * NV + k]; SB[m][k] = 0.0; }  // the sweep adds into SB
+  for (int k = 0; k < NV; ++k) FB[k] = Fb[k];
+  interface_flux_vjp<double, NV>(SS, st, 0, FB, SB);
+  for (int m = 0; m < 6; ++m)
+    for (int k = 0; k < NV; ++k) Sb[m * NV + k] = SB[m][k];
+}
+
 extern "C" {
 
 // Midpoint flux of the interface between cells 2 and 3 of S[6][nvar] (x normal, Euler),
@@ -45,6 +58,16 @@ int host_interface_flux(int nvar, int weights, int flux, int characteristic, int
 double host_weno_side(int weights, int zp, double xi, double eps, const double* v, double* wz, double* wf) {
   const SchemeT<double> st = make_scheme(0, weights, 0, 0, zp, 0, xi, eps, 0.0);
   return weno_side<double, 0>(v[0], v[1], v[2], v[3], v[4], st, wz, wf);
+}
+
+// Reverse sweep of the interface flux: Sb[6][nvar] = (dF/dS)^T Fb for the flux of
+// host_interface_flux with the same options.  Returns -1 on an unsupported nvar.
+int host_interface_flux_vjp(int nvar, int weights, int flux, int characteristic, int zp, double xi, double eps,
+                            double alpha, const double* S, const double* Fb, double* Sb) {
+  const SchemeT<double> st = make_scheme(1, weights, flux, characteristic, zp, 0, xi, eps, alpha);
+  if (nvar == 3) { vjp_nv<3>(st, S, Fb, Sb); return 0; }
+  if (nvar == 4) { vjp_nv<4>(st, S, Fb, Sb); return 0; }
+  return -1;
 }
 
 // Eq. 3 (WCNS family) or the two-point difference (WENO family) of six midpoint fluxes

@@ -16,7 +16,10 @@ rounding (the GPU parity tests compare those).  Checked here, interface by inter
   evaluating Eq. 20, the final weights equal the oracle's full evaluation exactly, and
   stencils whose weights leave the plateau gradually get the full map's weights;
 * the flux difference of Eq. 3 differentiates polynomial fluxes of degree up to 6
-  exactly at the cell centre (closed form; the two-point difference of App. B, degree 2).
+  exactly at the cell centre (closed form; the two-point difference of App. B, degree 2);
+* the adjoint's reverse sweep of one interface flux (`interface_flux_vjp`,
+  wcns_adjoint.cuh) is the transpose of the forward flux's derivative: dot products
+  against fourth-order central differences of the host-built forward flux.
 """
 import ctypes
 import os
@@ -54,6 +57,8 @@ def host():
     L.host_weno_side.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, DP, DP, DP]
     L.host_flux_difference.restype = ctypes.c_double
     L.host_flux_difference.argtypes = [ctypes.c_int, DP, ctypes.c_double]
+    L.host_interface_flux_vjp.restype = ctypes.c_int
+    L.host_interface_flux_vjp.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 3 + [DP, DP, DP]
     yield L
     shutil.rmtree(d, ignore_errors=True)
 
@@ -244,3 +249,60 @@ def test_ratio_bound_on_stencils_built_for_its_edge(host, zp):
             val = host.host_weno_side(WEIGHTS["FE"], zp, 1e6, 1e-40, v.ctypes.data_as(DP), None, None)
             assert abs(val - vo) <= 1e-10, (d3, mirror, val, vo)
     assert off > 100  # the sweep crosses the plateau edge
+
+
+VJP_CASES = [  # weights, p, xi, stencil noise, difference step, tolerance
+    ("JS", 1, 1e6, 0.05, 1e-5, 2e-6), ("JS", 2, 1e6, 0.05, 1e-5, 2e-6), ("Z", 2, 1e6, 0.05, 1e-5, 2e-6),
+    # at xi = 100 the map is steep next to the ideal weights: differences need small steps
+    ("FE", 2, 100.0, 0.05, 1e-7, 2e-6), ("PFE", 2, 100.0, 0.05, 1e-7, 2e-6),
+    # at xi = 1e6 the map is a staircase: smooth stencils sit on its flat plateaus
+    ("FE", 1, 1e6, 0.0, 1e-6, 1e-7), ("FE", 2, 1e6, 0.0, 1e-6, 1e-7),
+]
+
+
+@pytest.mark.parametrize("weights,zp,xi,noise,step,tol", VJP_CASES)
+def test_interface_flux_vjp_is_the_transposed_derivative(host, weights, zp, xi, noise, step, tol):
+    """<Sb, dS> with Sb = (dF/dS)^T Fb from the reverse sweep equals <Fb, dF/dS dS> from
+    central differences of the forward flux (LLF with frozen alpha, the adjoint's flux;
+    eps = 1e-6 as in the adjoint tests, where the Z weights stay differentiable).  A sample
+    whose difference quotients at two steps disagree has a switch (the PFE box, a kink of
+    the weights) within the step and is skipped; at most a quarter are."""
+    rng = np.random.default_rng(zlib.crc32(repr((weights, zp, xi)).encode()))
+    x = np.arange(6, dtype=np.float64)
+
+    def flux(S, nvar, ch):
+        F = np.zeros(nvar)
+        S = np.ascontiguousarray(S)
+        host.host_interface_flux(nvar, WEIGHTS[weights], FLUXES["LLF_FROZEN"], ch, zp, 0, xi, 1e-6, 1.7, 0,
+                                 S.ctypes.data_as(DP), F.ctypes.data_as(DP))
+        return F
+
+    def quotient(S, dS, nvar, ch, e):
+        return (-flux(S + 2 * e * dS, nvar, ch) + 8 * flux(S + e * dS, nvar, ch)
+                - 8 * flux(S - e * dS, nvar, ch) + flux(S - 2 * e * dS, nvar, ch)) / (12 * e)
+
+    checked = skipped = 0
+    for nvar in (3, 4):
+        for ch in (0, 1):
+            for _ in range(8):
+                ph = rng.uniform(0, 6)
+                rho = 1 + 0.2 * np.sin(0.5 * x + ph) + noise * rng.normal(size=6)
+                u = 0.3 + 0.2 * np.cos(0.4 * x + ph)
+                v = 0.1 * np.sin(0.3 * x)
+                p = 1 + 0.2 * np.sin(0.45 * x + 1)
+                S = np.ascontiguousarray(inputs.prim_to_cons(rho, u, v, p, 1.4, 1 if nvar == 3 else 2).T)
+                Fb, dS = rng.normal(size=nvar), rng.normal(size=S.shape)
+                Sb = np.zeros_like(S)
+                assert host.host_interface_flux_vjp(nvar, WEIGHTS[weights], FLUXES["LLF_FROZEN"], ch, zp, xi, 1e-6,
+                                                    1.7, S.ctypes.data_as(DP), Fb.ctypes.data_as(DP),
+                                                    Sb.ctypes.data_as(DP)) == 0
+                scale = 1e-3 * np.abs(Fb).sum()
+                rhs = (Fb * quotient(S, dS, nvar, ch, step)).sum()
+                rhs2 = (Fb * quotient(S, dS, nvar, ch, step / 2)).sum()
+                if abs(rhs - rhs2) > tol * (abs(rhs2) + scale):
+                    skipped += 1
+                    continue
+                checked += 1
+                lhs = (Sb * dS).sum()
+                assert abs(lhs - rhs2) <= tol * (abs(rhs2) + scale), (nvar, ch, lhs, rhs2)
+    assert skipped * 3 <= checked, (checked, skipped)
