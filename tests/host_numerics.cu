@@ -42,12 +42,16 @@ static void vjp_nv(const SchemeT<double>& st, const double* S, const double* Fb,
 
 extern "C" {
 
-// Midpoint flux of the interface between cells 2 and 3 of S[6][nvar] (x normal, Euler),
-// with run-time options (fixed = 0) or the compiled default configuration (fixed = 1).
-// Returns 1 if the interface fell back to (U_i, U_{i+1}), -1 on an unsupported nvar.
+// Midpoint flux of the interface between cells 2 and 3 of S[6][nvar] (x normal): Euler
+// for nvar = 3 or 4 (alpha: the frozen Lax-Friedrichs speed), scalar advection with speed
+// alpha for nvar = 1; run-time options (fixed = 0) or the compiled default configuration
+// (fixed = 1, Euler only).  Returns 1 if the interface fell back to (U_i, U_{i+1}), -1 on
+// an unsupported nvar.
 int host_interface_flux(int nvar, int weights, int flux, int characteristic, int zp, int family, double xi,
                         double eps, double alpha, int fixed, const double* S, double* F) {
-  const SchemeT<double> st = make_scheme(1, weights, flux, characteristic, zp, family, xi, eps, alpha);
+  const SchemeT<double> st =
+      make_scheme(nvar == 1 ? 0 : 1, weights, flux, characteristic, zp, family, xi, eps, alpha);
+  if (nvar == 1) return flux_nv<1, 0>(st, S, F);
   if (nvar == 3) return fixed ? flux_nv<3, 1>(st, S, F) : flux_nv<3, 0>(st, S, F);
   if (nvar == 4) return fixed ? flux_nv<4, 1>(st, S, F) : flux_nv<4, 0>(st, S, F);
   return -1;

@@ -306,3 +306,29 @@ def test_interface_flux_vjp_is_the_transposed_derivative(host, weights, zp, xi, 
                 lhs = (Sb * dS).sum()
                 assert abs(lhs - rhs2) <= tol * (abs(rhs2) + scale), (nvar, ch, lhs, rhs2)
     assert skipped * 3 <= checked, (checked, skipped)
+
+
+@pytest.mark.parametrize("weights", list(WEIGHTS))
+@pytest.mark.parametrize("family", [0, 1])
+def test_scalar_advection_flux_matches_the_oracle(host, weights, family):
+    """u_t + a u_x = 0 (Sec. 2): the upwind interpolated state times a (WCNS family) or the
+    split flux reconstruction (App. B), for a of both signs, on smooth, jump and random
+    stencils."""
+    rng = np.random.default_rng(zlib.crc32(repr((weights, family)).encode()))
+    x = np.arange(6, dtype=np.float64)
+    for a in (1.0, -0.7):
+        for kind in range(3):
+            for _ in range(10):
+                if kind == 0:
+                    S = np.sin(0.4 * x + rng.uniform(0, 6))
+                elif kind == 1:
+                    S = np.where(x < rng.integers(1, 6), 1.0, 0.0) + 0.01 * rng.normal(size=6)
+                else:
+                    S = rng.normal(size=6)
+                S = np.ascontiguousarray(S.reshape(6, 1))
+                F = np.zeros(1)
+                host.host_interface_flux(1, WEIGHTS[weights], 0, 0, 1, family, 1e6, 1e-40, a, 0,
+                                         S.ctypes.data_as(DP), F.ctypes.data_as(DP))
+                Fo, _ = oracle.interface_flux(S, 1, system=0, ax=a, weights=weights,
+                                              family="WENO" if family else "WCNS")
+                assert abs(F[0] - Fo[0]) <= 1e-13 * (1 + abs(Fo[0])), (a, kind, F, Fo)
