@@ -74,6 +74,24 @@ int host_interface_flux_vjp(int nvar, int weights, int flux, int characteristic,
   return -1;
 }
 
+// Ghost or interior value of component v at cell m of line `line` in direction dir, with
+// the boundary faces types[4] (x-lo, x-hi, y-lo, y-hi; active if any is not the grid's bc)
+// and their states ua, ub (conservative, storage ordering), at the state's time.
+double host_face_cell(const double* u, int64_t pitch, int64_t fstride, int dir, int64_t line, int64_t m, int64_t n,
+                      int bc, int v, const int* types, const double* ua, const double* ub, double wall_x, double x0,
+                      double dxdy, double speed, double lo_x, double lo_y, double hx, double hy, double time) {
+  Faces<double> f{};
+  for (int k = 0; k < 4; ++k) {
+    f.type[k] = types[k];
+    f.ua[k] = ua[k];
+    f.ub[k] = ub[k];
+    if (types[k] != kFaceGrid) f.active = 1;
+  }
+  f.wall_x = wall_x; f.x0 = x0; f.dxdy = dxdy; f.speed = speed;
+  f.lo_x = lo_x; f.lo_y = lo_y; f.hx = hx; f.hy = hy;
+  return face_cell<double>(u, pitch, fstride, dir, line, m, n, bc, v, f, time);
+}
+
 // Eq. 3 (WCNS family) or the two-point difference (WENO family) of six midpoint fluxes
 // f[0..5] = F_{i-5/2} .. F_{i+5/2}, divided by h = 1 / inv_h.
 double host_flux_difference(int family, const double* f, double inv_h) {

@@ -19,7 +19,10 @@ rounding (the GPU parity tests compare those).  Checked here, interface by inter
   exactly at the cell centre (closed form; the two-point difference of App. B, degree 2);
 * the adjoint's reverse sweep of one interface flux (`interface_flux_vjp`,
   wcns_adjoint.cuh) is the transpose of the forward flux's derivative: dot products
-  against fourth-order central differences of the host-built forward flux.
+  against fourth-order central differences of the host-built forward flux;
+* the ghost cells of the boundary faces (`face_cell`, Sec. 4.3) follow their
+  definitions: mirror cells with the normal momentum reversed at walls, the edge cell for
+  outflow, the grid's wrap, fixed states, and the exact moving shock at ghost-cell centres.
 """
 import ctypes
 import os
@@ -58,6 +61,10 @@ def host():
     L.host_flux_difference.restype = ctypes.c_double
     L.host_flux_difference.argtypes = [ctypes.c_int, DP, ctypes.c_double]
     L.host_interface_flux_vjp.restype = ctypes.c_int
+    L.host_face_cell.restype = ctypes.c_double
+    L.host_face_cell.argtypes = ([DP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), DP, DP]
+                                 + [ctypes.c_double] * 9)
     L.host_interface_flux_vjp.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 3 + [DP, DP, DP]
     yield L
     shutil.rmtree(d, ignore_errors=True)
@@ -332,3 +339,51 @@ def test_scalar_advection_flux_matches_the_oracle(host, weights, family):
                 Fo, _ = oracle.interface_flux(S, 1, system=0, ax=a, weights=weights,
                                               family="WENO" if family else "WCNS")
                 assert abs(F[0] - Fo[0]) <= 1e-13 * (1 + abs(Fo[0])), (a, kind, F, Fo)
+
+
+FACE_GRID, FACE_TRANS, FACE_WALL, FACE_FIXED, FACE_FIXED_THEN_WALL, FACE_SHOCK = range(6)
+
+
+def test_boundary_face_ghost_cells_follow_their_definitions(host):
+    nx, ny, pitch, nv = 13, 9, 16, 4
+    rng = np.random.default_rng(8)
+    u = np.ascontiguousarray(rng.uniform(0.5, 2.0, size=(nv, ny, pitch)))
+    lo, hx, hy = (0.1, -0.2), 1.0 / nx, 0.5 / ny
+    ua, ub = np.array([8.0, 57.1, -33.0, 563.5]), np.array([1.4, 0.0, 0.0, 2.5])
+    wall_x, x0, dxdy, speed, time = 1.0 / 6.0 + 0.1, 0.3, 1.0 / np.sqrt(3.0), 20.0, 0.013
+    tarr = (ctypes.c_int * 4)
+    cases = [(FACE_TRANS, FACE_WALL, FACE_FIXED_THEN_WALL, FACE_SHOCK), (FACE_FIXED, FACE_GRID, FACE_WALL, FACE_TRANS),
+             (FACE_GRID, FACE_GRID, FACE_GRID, FACE_GRID)]
+    for types in cases:
+        for dir_, n, nlines in ((0, nx, ny), (1, ny, nx)):
+            for bc in (0, 1):
+                if bc == 0 and any(t != FACE_GRID for t in types):
+                    continue  # periodic lines have no faces
+                for line in range(nlines):
+                    for m in list(range(-3, 0)) + list(range(n, n + 3)) + [0, n - 1]:
+                        for v in range(nv):
+                            got = host.host_face_cell(u.ctypes.data_as(DP), pitch, ny * pitch, dir_, line, m, n, bc, v,
+                                                      tarr(*types), ua.ctypes.data_as(DP), ub.ctypes.data_as(DP),
+                                                      wall_x, x0, dxdy, speed, lo[0], lo[1], hx, hy, time)
+
+                            def cell(k):
+                                return u[v, line, k] if dir_ == 0 else u[v, k, line]
+
+                            typ = types[2 * dir_ + (0 if m < 0 else 1)]
+                            # ghost-cell centre
+                            x = lo[0] + ((m if dir_ == 0 else line) + 0.5) * hx
+                            y = lo[1] + ((line if dir_ == 0 else m) + 0.5) * hy
+                            if 0 <= m < n:
+                                want = cell(m)
+                            elif typ == FACE_GRID:
+                                want = cell(m % n) if bc == 0 else cell(min(max(m, 0), n - 1))
+                            elif typ == FACE_TRANS:
+                                want = cell(min(max(m, 0), n - 1))
+                            elif typ == FACE_FIXED or (typ == FACE_FIXED_THEN_WALL and x < wall_x):
+                                want = ua[v]
+                            elif typ in (FACE_WALL, FACE_FIXED_THEN_WALL):
+                                mirror = -1 - m if m < 0 else 2 * n - 1 - m
+                                want = -cell(mirror) if v == 1 + dir_ else cell(mirror)
+                            else:  # moving oblique shock: state a behind x0 + (y + speed t) dxdy
+                                want = ua[v] if x < x0 + (y + speed * time) * dxdy else ub[v]
+                            assert got == want, (types, dir_, bc, line, m, v, got, want)
