@@ -176,6 +176,10 @@ inline double phi_ij(int i, int j) {
   return 1.0;
 }
 
+// Eq. 20: the mapping function of weight i, the weight plus one tanh step per null point
+// kappa (psi_{i,j} + psi_{i,j-1}), each of half the jump between consecutive control values
+// of Table 2 (Table B.2 for the App. B family; the weight itself on identity segments),
+// phi of Eq. 21 as printed.
 template <class R>
 R fe_map(int i, const R& w, double xi, double kappa, int family = 0) {
   const double(*ctrl)[5] = family == 1 ? kOmegaCtrlB : kOmegaCtrl;
@@ -319,6 +323,8 @@ struct Prim {
   R rho, un, ut, p, H, c2;
 };
 
+// Primitive variables of a conserved state (Sec. 2: ideal gas, p = (gamma - 1)(E - rho |v|^2 / 2)),
+// with the total enthalpy H and the squared sound speed.
 template <class R>
 Prim<R> primitive(const R* U, int nvar, double gamma) {
   Prim<R> s;
@@ -341,6 +347,7 @@ Prim<R> primitive(const R* U, int nvar, double gamma) {
   return s;
 }
 
+// Euler flux in the sweep normal (Eq. 1).
 template <class R>
 void physical_flux(const R* U, int nvar, double gamma, R* F) {
   Prim<R> s = primitive(U, nvar, gamma);
@@ -395,6 +402,8 @@ void eigenvectors(int nvar, double gamma, const R& u, const R& v, const R& H, co
   }
 }
 
+// Positive density and pressure: the admissibility test of an interpolated state (a
+// state that fails it falls back to the cell states U_i, U_{i+1} at that interface).
 template <class R>
 bool physical_state(const R* U, int nvar, double gamma) {
   if (!(val(U[0]) > 0.0)) return false;
@@ -762,6 +771,8 @@ void line_rhs(int64_t n, int bc, double h, const oracle_cfg& c, double alpha, co
   }
 }
 
+// L(u) of Eq. 2 on the whole grid: the Eq. 3 difference of every x line, plus that of
+// every y line on 2D grids (dimension by dimension).
 template <class R>
 void rhs(const oracle_cfg& c, const R* u, R* dudt, Stats* st) {
   const int64_t nx = c.nx, ny = (c.ndim == 2) ? c.ny : 1;
@@ -813,6 +824,7 @@ void max_wave(const oracle_cfg& c, const double* u, double* wx, double* wy) {
   *wy = my;
 }
 
+// Step at CFL number cfl (Sec. 4 marches at a fixed CFL number): dt = cfl / sum_d max_d / h_d.
 double cfl_dt(const oracle_cfg& c, const double* u, double cfl) {
   double wx, wy;
   max_wave(c, u, &wx, &wy);
